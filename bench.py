@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 damped-acoustic propagator.
+
+One step = one forward shot of the 3D stencil sweep workload: 256^3 interior at
+10 m plus a 40-point damping layer (336^3 grid), 8 flat layers 1.5 -> 4.5 km/s,
+space order 8, dt = 0.9 x CFL, 1000 time steps, one 15 Hz Ricker source and
+128 x 128 off-grid receivers (coefficient setup, stencil, injection,
+interpolation and the time loop all run in the CUDA library).
+
+value  = grid points updated per second over all ranks (Gpts/s), inputs resident
+         in HBM, device-timed with CUDA events.
+e2e    = same metric through the host-array C-ABI call (m, eta, wavelet copied in
+         from pinned host memory and the receiver data copied out every step).
+roofline: the stencil kernel's compulsory bytes per launch over its live average
+         duration (CUDA events on the library's stream), against the measured
+         HBM copy bandwidth.
+cpu_baseline / --impl reference: the FP64 CPU oracle on a bounded sample.
+
+Multi-GPU (torchrun): replicas only (one independent shot per GPU, no collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpts/s & %HBM roofline, SO8 3D acoustic; shots/h + p99 served vs plain"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--space-order", type=int, default=8)
+    p.add_argument("--nt", type=int, default=1000)
+    p.add_argument("--n", type=int, default=256, help="interior points per axis")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def workload(args):
+    from paper_1808_01995_gb300 import synth
+    model = synth.layers_3d(space_order=args.space_order, n=args.n, nt=args.nt)
+    return model
+
+
+def describe(model, nt, dt):
+    n = model.shape
+    return {"workload": f"layers3d {model.shape[0] - 2 * model.nbl}^3 + {model.nbl}-pt layer ({n[0]}x{n[1]}x{n[2]}) "
+                        f"SO{model.space_order} forward, nt={nt}, 1 Ricker source, {len(model.rec)} receivers",
+            "grid": list(n), "space_order": model.space_order, "nt": nt, "dt_s": dt,
+            "l2": "inputs larger than L2 (four 4-byte fields of the grid per step)",
+            "parallelism": "replicas (one shot per GPU)"}
+
+
+def algorithmic_bytes_per_launch(model):
+    """Compulsory stencil bytes of one time step: read u^n, u^{n-1}, b, write u^{n+1}
+    (16 B per point) plus s (4 B) where eta != 0."""
+    npts = int(np.prod(model.shape))
+    ndamp = int(np.count_nonzero(model.eta))
+    return 16 * npts + 4 * ndamp, npts, ndamp
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic(space_order, grid):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"stencil3d_fwd_so{space_order}_{grid}.md")
+    if not os.path.exists(path):
+        return None
+    src = open(os.path.join(ROOT, "paper_1808_01995_gb300", "csrc", "stencil3d.cuh"), "rb").read()
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("stencil3d.cuh sha256[:16]") != sha:
+        return None
+    try:
+        return float(vals["dram bytes per launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# oracle legs (CPU)
+# ---------------------------------------------------------------------------
+def oracle_sample(model, dt, budget_s):
+    """Time the FP64 oracle's forward on the same grid for a bounded number of time
+    steps; returns (Gpts/s, steps, seconds, threads)."""
+    import oracle as O
+    nthreads = O.num_threads()
+    k = model.space_order
+    steps = 1
+    while True:
+        g = O.Grid(model.shape, model.spacing, model.origin, k, dt, steps)
+        q = model.wavelet(dt, steps)
+        t0 = time.perf_counter()
+        O.forward(g, model.m32(), model.eta32(), q, model.src, model.rec)
+        el = time.perf_counter() - t0
+        if el >= 0.5 * budget_s or steps >= 4096:
+            break
+        steps = max(steps + 1, min(steps * 8, int(steps * 0.6 * budget_s / max(el, 1e-3))))
+    return np.prod(model.shape) * steps / el / 1e9, steps, el, nthreads
+
+
+def run_reference(args):
+    world, rank, local = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return
+    from paper_1808_01995_gb300 import synth  # noqa: F401  (inputs only)
+    import oracle as O
+    model = workload(args)
+    dt = 0.9 * O.cfl_dt(model.spacing, args.space_order, model.vmax)
+    per_step = max(1.0, args.cpu_seconds / max(args.steps, 1))
+    vals = []
+    nthreads = O.num_threads()
+    steps_used = 0
+    for i in range(args.warmup + args.steps):
+        rate, steps, el, nthreads = oracle_sample(model, dt, per_step if i >= args.warmup else 0.5)
+        if i >= args.warmup:
+            vals.append(rate)
+            steps_used = steps
+    v = float(np.median(vals))
+    sample = (f"FP64 oracle forward on the full {model.shape} grid for {steps_used} of {args.nt} time steps "
+              f"per step (rate scales linearly in steps)")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gpts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": np.prod(model.shape) * args.nt / (v * 1e9) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": describe(model, args.nt, dt),
+            "cpu_baseline": {"value": v, "unit": "Gpts/s", "cores": nthreads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    world, rank, local = dist_init()
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1808_01995_gb300 import build as B
+    from paper_1808_01995_gb300 import wavprop as W
+    if rank == 0 or not B.up_to_date():
+        B.build()
+    barrier(world)
+    model = workload(args)
+    k = args.space_order
+    grid0 = W.Grid(model.shape, model.spacing, model.origin, k)
+    dt = 0.9 * W.wp_cfl_dt(grid0, model.vmax)
+    nt = args.nt
+    grid = W.Grid(model.shape, model.spacing, model.origin, k, dt, nt)
+    ctx = W.Context(local)
+    h = ctx.handle
+    m = torch.from_numpy(model.m32()).cuda()
+    eta = torch.from_numpy(model.eta32()).cuda()
+    q = torch.from_numpy(model.wavelet(dt, nt)).cuda()
+    rec = torch.zeros((nt, len(model.rec)), device="cuda")
+    src_c, rec_c = model.src, model.rec
+
+    def step():
+        W.wp_forward_dev(h, grid, m, eta, q, src_c, rec_c, rec)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    W.wp_set_profiling(h, True)
+    W.wp_profile_read(h, reset=True)
+    launches0 = W.wp_kernel_launches(h)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            step()
+        ev1.record()
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = W.wp_kernel_launches(h) - launches0
+    k_ms, k_n = W.wp_profile_read(h, reset=True)
+    W.wp_set_profiling(h, False)
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ms, world)
+    npts = int(np.prod(model.shape))
+    value = world * npts * nt * args.steps / (ms * 1e-3) / 1e9
+
+    alg_bytes, _, ndamp = algorithmic_bytes_per_launch(model)
+    peak, peak_kind = measured_peaks()
+    k_avg_s = (k_ms / max(k_n, 1)) * 1e-3
+    achieved = alg_bytes / k_avg_s / 1e9
+    traffic = kernel_traffic(k, "x".join(str(s) for s in model.shape))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": f"stencil3d_kernel<R={k // 2},fwd>",
+                "kernel_avg_us": k_avg_s * 1e6, "alg_bytes_per_launch": alg_bytes,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
+
+    e2e = None
+    if not args.no_e2e:
+        mh = torch.from_numpy(model.m32()).pin_memory()
+        eh = torch.from_numpy(model.eta32()).pin_memory()
+        qh = torch.from_numpy(model.wavelet(dt, nt)).pin_memory()
+        mhn, ehn, qhn = mh.numpy(), eh.numpy(), qh.numpy()
+        out_h = torch.empty((nt, len(model.rec)), dtype=torch.float32).pin_memory().numpy()
+        lib = W.lib()
+        import ctypes
+        g = grid.c()
+        src_a = np.ascontiguousarray(src_c, dtype=np.float64)
+        rec_a = np.ascontiguousarray(rec_c, dtype=np.float64)
+
+        def e2e_step():
+            rc = lib.wp_forward(h, ctypes.byref(g), mhn.ctypes.data, ehn.ctypes.data, qhn.ctypes.data, len(src_a),
+                                src_a.ctypes.data, len(rec_a), rec_a.ctypes.data, out_h.ctypes.data)
+            if rc != 0:
+                raise RuntimeError(W.wp_last_error())
+
+        e2e_step()
+        torch.cuda.synchronize()
+        ke = max(1, min(args.steps, 3))
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            e2e_step()
+        torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": world * npts * nt * ke / el / 1e9, "unit": "Gpts/s",
+               "h2d_bytes_per_step": int(mhn.nbytes + ehn.nbytes + qhn.nbytes),
+               "d2h_bytes_per_step": int(out_h.nbytes), "steps": ke,
+               "call": "wp_forward (host arrays, pinned)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, steps, el, nthreads = oracle_sample(model, dt, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "Gpts/s", "cores": nthreads, "kind": "oracle",
+               "sample": f"FP64 oracle forward on the full grid, {steps} of {nt} time steps ({el:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": describe(model, nt, dt),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * wavprop.h -- C ABI of the GB300 (sm_103a) propagator for the damped isotropic
+ * acoustic wave equation
+ *
+ *      m u_tt - Lap u + eta u_t = q,      m = 1 / c^2            (Eq. acoustic, Eq. fdWE-abc)
+ *
+ * discretised with a space-order-k central Laplacian (Eq. fdSpace), the
+ * second-order leapfrog in time (Eq. fdTime, Eq. eulerfwd) and a central
+ * difference for the damping term, i.e. per time step
+ *
+ *      (m + eta dt/2) u^{n+1} = (2m + dt^2 Lap) u^n - (m - eta dt/2) u^{n-1} + dt^2 P_s^T q^n,
+ *      d^n = P_r u^{n+1},      u^{-1} = u^0 = 0,
+ *
+ * with zero values outside the grid (Sec. 3.2), multilinear injection P_s^T and
+ * interpolation P_r inside the containing cell (Sec. 2.2.4), the adjoint as
+ * backward substitution with the transposed system (Sec. 2.2.2, Eq. Adj) and the
+ * adjoint-state gradient of J(m) = 1/2 ||F(m) q - d_obs||^2 (Eq. AS, Eq. Grad).
+ *
+ * Conventions shared by every call
+ *   - Fields are C-ordered arrays of float: (nz, ny, nx) in 3D, (nz, nx) in 2D,
+ *     x fastest.  The grid is the computational grid (physical interior plus any
+ *     damping layer).
+ *   - spacing[], origin[] and point coordinates use the same axis order as
+ *     shape[] (z, y, x) / (z, x); origin is the coordinate of index 0.
+ *   - A point must lie in [origin, origin + (n-1) h] on every axis (points within
+ *     1e-9 cells outside are clamped onto the grid).  Its cell is
+ *     i = min(floor((c - o)/h), n - 2), computed in double precision.
+ *   - Time series are row-major [nt][npoints] float arrays; sample n of a
+ *     receiver trace is u^{n+1} (time (n+1) dt).
+ *   - The injected source is weighted by dt^2 / (m + eta dt/2) at each corner
+ *     (equal to the paper's dt^2/m where eta = 0).
+ *
+ * Ownership: the caller owns every array passed in or out; the library reads or
+ * writes them during the call and keeps no reference.  A context owns its device
+ * memory, stream and kernels' scratch; a wp_state owns its snapshots.
+ *
+ * Errors: every int-returning call returns WP_OK (0) or a negative status and
+ * sets a thread-local message readable with wp_last_error().  No call throws.
+ * Calls are synchronous: they return after their device work has finished.
+ * A context may be used by one thread at a time; distinct contexts may run
+ * concurrently from different threads (each has its own stream).
+ */
+#ifndef WAVPROP_H
+#define WAVPROP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WP_OK 0
+#define WP_EINVAL (-1)      /* bad shape/order/count/coordinate, m <= 0 or eta < 0 */
+#define WP_ECFL (-2)        /* dt above the stability limit of the scheme */
+#define WP_ENOMEM (-3)      /* request exceeds the context's HBM budget or device memory */
+#define WP_ENONFINITE (-4)  /* NaN or Inf in an input array */
+#define WP_ECUDA (-5)       /* a CUDA runtime or driver call failed */
+#define WP_ETIMEOUT (-6)    /* device work did not finish within the context's deadline */
+#define WP_EDEVICE (-7)     /* a kernel reported an internal error (e.g. a wait that timed out) */
+
+/* hbm_budget_bytes value meaning "90 % of the device memory free at creation" */
+#define WP_BUDGET_AUTO ((size_t)-1)
+
+typedef struct wp_ctx wp_ctx;
+typedef struct wp_state wp_state;
+
+typedef struct {
+  int ndim;            /* 2 or 3 */
+  int64_t shape[3];    /* (nz, ny, nx) or (nz, nx); every used entry >= 2 */
+  double spacing[3];   /* > 0, same axis order */
+  double origin[3];    /* coordinate of index 0, same axis order */
+  int space_order;     /* k, even, 2..16 */
+  double dt;           /* time step, 0 < dt <= wp_cfl_dt(...) */
+  int nt;              /* number of time steps, >= 0 */
+} wp_grid;
+
+/* Create a context on CUDA device `device` that may hold at most
+ * hbm_budget_bytes of device memory (WP_BUDGET_AUTO: 90 % of free memory).
+ * *out receives the context; release it with wp_destroy. */
+int wp_create(wp_ctx **out, int device, size_t hbm_budget_bytes);
+void wp_destroy(wp_ctx *ctx);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *wp_last_error(void);
+
+/* Seconds after which a call gives up waiting for its device work and returns
+ * WP_ETIMEOUT (default 600).  The context must not be reused after a timeout. */
+int wp_set_timeout(wp_ctx *ctx, double seconds);
+
+/* Weights a_0..a_{k/2} of the order-k central second derivative
+ * (Eq. fdSpace, centre counted once): closed form
+ * a_j = 2 (-1)^{j+1} (p!)^2 / (j^2 (p-j)! (p+j)!), p = k/2, a_0 = -2 sum a_j.
+ * alpha must hold k/2 + 1 doubles. */
+int wp_fd_weights(int space_order, double *alpha);
+
+/* Largest stable dt of the scheme for velocity vmax (von Neumann bound of the
+ * undamped leapfrog: dt_max = 2 / (vmax sqrt(sum_a A_k / h_a^2)), A_k = |a_0| + 2 sum |a_j|). */
+int wp_cfl_dt(const wp_grid *grid, double vmax, double *dt_max);
+
+/* Device bytes a call would hold for this grid: mode 0 forward/adjoint,
+ * 1 gradient with the given snapshot interval. */
+int wp_estimate_bytes(const wp_grid *grid, int nsrc, int nrec, int mode, int snap_interval,
+                      size_t *bytes);
+
+/* ---- forward, adjoint, gradient: HOST arrays ---------------------------- */
+
+/* Forward modelling (Sec. 3.2): rec_out[nt][nrec] = P_r u^{n+1}.
+ * m, eta: fields (host, float); wavelet[nt][nsrc]; src_coords[nsrc][ndim] and
+ * rec_coords[nrec][ndim] (double).  nsrc, nrec >= 0. */
+int wp_forward(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *eta,
+               const float *wavelet, int nsrc, const double *src_coords, int nrec,
+               const double *rec_coords, float *rec_out);
+
+/* Adjoint modelling (Sec. 3.3, Eq. Adj): the exact transpose of the forward map
+ * wavelet -> rec_out.  rec_data[nt][nrec] is injected at the receivers backward in
+ * time; src_out[nt][nsrc] samples the adjoint field at the sources. */
+int wp_adjoint(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *eta,
+               const float *rec_data, int nrec, const double *rec_coords, int nsrc,
+               const double *src_coords, float *src_out);
+
+/* Gradient of J(m) = 1/2 ||F(m) q - d_obs||^2 (Eq. AS, Eq. Grad) given the
+ * residual F(m) q - d_obs [nt][nrec]:
+ *   grad = -dt^-2 sum_{j=1}^{nt} u^j (w^j - 2 w^{j+1} + w^{j+2}),
+ * w the adjoint field driven by the residual.  The forward field is kept as
+ * snapshot pairs every snap_interval steps in device memory and recomputed
+ * between them (Sec. 3.3, checkpointing).  grad_out has the field's shape. */
+int wp_gradient(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *eta,
+                const float *wavelet, int nsrc, const double *src_coords,
+                const float *residual, int nrec, const double *rec_coords, int snap_interval,
+                float *grad_out);
+
+/* ---- DEVICE-array variants ------------------------------------------------
+ * Same contracts; m, eta, wavelet, rec/src data and outputs are device pointers
+ * (contiguous, float), coordinates stay on the host.  Work is ordered after
+ * everything already queued on `stream` (a cudaStream_t, NULL = legacy default
+ * stream), and later work on `stream` is ordered after it. */
+int wp_forward_dev(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *eta,
+                   const float *wavelet, int nsrc, const double *src_coords, int nrec,
+                   const double *rec_coords, float *rec_out, void *stream);
+int wp_adjoint_dev(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *eta,
+                   const float *rec_data, int nrec, const double *rec_coords, int nsrc,
+                   const double *src_coords, float *src_out, void *stream);
+int wp_gradient_dev(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *eta,
+                    const float *wavelet, int nsrc, const double *src_coords,
+                    const float *residual, int nrec, const double *rec_coords,
+                    int snap_interval, float *grad_out, void *stream);
+
+/* nsteps source-free updates of (u_prev, u) = (u^{n-1}, u^n) in place (device
+ * fields, contiguous): on return they hold (u^{n+nsteps-1}, u^{n+nsteps}). */
+int wp_propagate_dev(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *eta,
+                     float *u_prev, float *u, int nsteps, void *stream);
+
+/* ---- split forward / backward (autograd, serving) ---------------------------
+ * wp_forward_save runs the forward (device arrays) and keeps its snapshots
+ * resident in *state; wp_backward(state, residual, grad) then returns
+ * J^T residual = dJ/dm for J = 1/2 ||d - d_obs||^2 with residual = d - d_obs
+ * (or any upstream gradient dL/dd).  A state may be back-propagated more than
+ * once; wp_state_free releases its memory.  The state borrows ctx: free it
+ * before wp_destroy(ctx), and do not use ctx for another call in between if
+ * memory is tight (the state's memory counts against ctx's budget). */
+int wp_forward_save(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *eta,
+                    const float *wavelet, int nsrc, const double *src_coords, int nrec,
+                    const double *rec_coords, int snap_interval, float *rec_out, void *stream,
+                    wp_state **state);
+int wp_backward(wp_state *state, const float *residual, float *grad_out, void *stream);
+void wp_state_free(wp_state *state);
+
+/* Device bytes currently held by the context (including live states). */
+size_t wp_bytes_in_use(const wp_ctx *ctx);
+
+/* Number of kernels this context has launched (graph replays count every node). */
+uint64_t wp_kernel_launches(const wp_ctx *ctx);
+
+/* Profiling: while enabled, every stencil (K1) launch is bracketed by CUDA events
+ * on the context's stream; wp_profile_read returns the summed device time (ms)
+ * and the number of bracketed launches since the last reset. */
+int wp_set_profiling(wp_ctx *ctx, int enabled);
+int wp_profile_read(wp_ctx *ctx, double *stencil_ms, uint64_t *stencil_launches, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WAVPROP_H */

@@ -1,0 +1,1116 @@
+// Host side of the propagator library: contexts with a budgeted caching device
+// allocator, the pitched field layout, TMA descriptors, sparse-point setup,
+// the time loops (forward, adjoint, forward with snapshots, backward with
+// recompute + fused gradient), and the C ABI declared in wavprop.h.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/wavprop.h"
+#include "kernels.cuh"
+#include "stencil3d.cuh"
+
+using namespace wp;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CU(x)                                                                                  \
+  do {                                                                                         \
+    cudaError_t e_ = (x);                                                                      \
+    if (e_ != cudaSuccess) return fail(WP_ECUDA, "%s failed: %s", #x, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define TRY(x)              \
+  do {                      \
+    int rc_ = (x);          \
+    if (rc_ != WP_OK) return rc_; \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct wp_ctx {
+  int device = 0;
+  int num_sms = 0;
+  size_t budget = 0;
+  size_t in_use = 0;                       // live + cached device bytes
+  std::multimap<size_t, void *> cache;     // free blocks by size
+  std::map<void *, size_t> live;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_done = nullptr;
+  double timeout_s = 600.0;
+  int *d_scalars = nullptr;                // [0] error word, [1] bad-input bits, [2] max(1/m) bits
+  int *h_scalars = nullptr;                // pinned mirror
+  uint64_t launches = 0;
+  int smem3d[2][9] = {};
+  int occ3d[2][9] = {};
+  bool broken = false;
+  // profiling: an event pair around every stencil launch, summed on read
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_events;   // 2 per launch
+  size_t prof_used = 0;
+  double prof_ms = 0.0;
+  uint64_t prof_count = 0;
+};
+
+static size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static void release_cache(wp_ctx *c, size_t need) {
+  while (!c->cache.empty() && (need == 0 || c->in_use + need > c->budget)) {
+    auto it = std::prev(c->cache.end());
+    cudaFree(it->second);
+    c->in_use -= it->first;
+    c->cache.erase(it);
+  }
+}
+
+static int dev_alloc(wp_ctx *c, size_t bytes, void **out) {
+  bytes = round_up(std::max<size_t>(bytes, 1), 256);
+  auto it = c->cache.lower_bound(bytes);
+  if (it != c->cache.end() && it->first <= 2 * bytes) {
+    *out = it->second;
+    c->live[*out] = it->first;
+    c->cache.erase(it);
+    return WP_OK;
+  }
+  if (c->in_use + bytes > c->budget) release_cache(c, bytes);
+  if (c->in_use + bytes > c->budget)
+    return fail(WP_ENOMEM, "request of %zu bytes exceeds the context budget (%zu of %zu bytes in use)",
+                bytes, c->in_use, c->budget);
+  cudaError_t e = cudaMalloc(out, bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    release_cache(c, 0);
+    e = cudaMalloc(out, bytes);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *out = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? WP_ENOMEM : WP_ECUDA, "cudaMalloc(%zu) failed: %s", bytes,
+                cudaGetErrorString(e));
+  }
+  c->in_use += bytes;
+  c->live[*out] = bytes;
+  return WP_OK;
+}
+
+static void dev_free(wp_ctx *c, void *p) {
+  if (!p) return;
+  auto it = c->live.find(p);
+  if (it == c->live.end()) return;
+  c->cache.emplace(it->second, p);
+  c->live.erase(it);
+}
+
+// Allocations released (to the context cache) at scope exit.
+struct Arena {
+  wp_ctx *c;
+  std::vector<void *> ptrs;
+  explicit Arena(wp_ctx *c_) : c(c_) {}
+  ~Arena() {
+    for (void *p : ptrs) dev_free(c, p);
+  }
+  template <class T>
+  int alloc(T **out, size_t count) {
+    void *p = nullptr;
+    TRY(dev_alloc(c, count * sizeof(T), &p));
+    ptrs.push_back(p);
+    *out = static_cast<T *>(p);
+    return WP_OK;
+  }
+  void release_all_to(std::vector<void *> &dst) {
+    dst.insert(dst.end(), ptrs.begin(), ptrs.end());
+    ptrs.clear();
+  }
+};
+
+// Wait for everything queued on the context stream, with a deadline.
+static int ctx_wait(wp_ctx *c) {
+  CU(cudaEventRecord(c->ev_done, c->stream));
+  const auto t0 = std::chrono::steady_clock::now();
+  int spins = 0;
+  while (true) {
+    cudaError_t e = cudaEventQuery(c->ev_done);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return fail(WP_ECUDA, "device work failed: %s", cudaGetErrorString(e));
+    const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (dt > c->timeout_s) {
+      c->broken = true;
+      return fail(WP_ETIMEOUT, "device work did not finish within %.1f s", c->timeout_s);
+    }
+    if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(spins > 1000 ? 200 : 20));
+  }
+  return WP_OK;
+}
+
+static int check_device_error(wp_ctx *c) {
+  CU(cudaMemcpyAsync(c->h_scalars, c->d_scalars, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  TRY(ctx_wait(c));
+  if (c->h_scalars[0] != 0)
+    return fail(WP_EDEVICE, "a kernel reported device error %d (a wait timed out)", c->h_scalars[0]);
+  return WP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// geometry, weights, CFL
+// ---------------------------------------------------------------------------
+struct Geom {
+  int ndim = 3;
+  int nz = 0, ny = 1, nx = 0;
+  int pitch = 0;
+  long long plane = 0;     // ny * pitch
+  long long nfield = 0;    // nz * plane (elements of a pitched field)
+  long long npoints = 0;   // nz * ny * nx
+  double h[3] = {1, 1, 1}; // z, y, x
+  double o[3] = {0, 0, 0};
+  int k = 0, R = 0;
+  double dt = 0;
+  int nt = 0;
+  int tiles_x = 1, tiles_y = 1;
+  FieldGeom fg() const {
+    FieldGeom g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.pitch = pitch;
+    g.plane = plane;
+    return g;
+  }
+  size_t field_bytes() const { return static_cast<size_t>(nfield) * sizeof(float); }
+};
+
+// a_j = 2 (-1)^{j+1} C(2p, p-j) / (j^2 C(2p, p)),  a_0 = -2 sum a_j   (p = k/2)
+static bool weights(int k, double *alpha) {
+  if (k < 2 || k > 16 || (k & 1)) return false;
+  const int p = k / 2;
+  auto binom = [](int n, int r) {
+    double v = 1.0;
+    for (int i = 1; i <= r; ++i) v = v * (n - r + i) / i;
+    return v;
+  };
+  const double cpp = binom(2 * p, p);
+  double sum = 0.0;
+  for (int j = 1; j <= p; ++j) {
+    alpha[j] = ((j & 1) ? 2.0 : -2.0) * binom(2 * p, p - j) / (double(j) * j * cpp);
+    sum += alpha[j];
+  }
+  alpha[0] = -2.0 * sum;
+  return true;
+}
+
+static double cfl_limit(const Geom &G, double vmax) {
+  double a[9];
+  weights(G.k, a);
+  double A = std::fabs(a[0]);
+  for (int j = 1; j <= G.R; ++j) A += 2.0 * std::fabs(a[j]);
+  double s = A / (G.h[0] * G.h[0]) + A / (G.h[2] * G.h[2]);
+  if (G.ndim == 3) s += A / (G.h[1] * G.h[1]);
+  return 2.0 / (vmax * std::sqrt(s));
+}
+
+static int make_geom(const wp_grid *g, Geom *G, bool need_dt = true) {
+  if (!g) return fail(WP_EINVAL, "grid is NULL");
+  if (g->ndim != 2 && g->ndim != 3) return fail(WP_EINVAL, "ndim must be 2 or 3 (got %d)", g->ndim);
+  if (g->space_order < 2 || g->space_order > 16 || (g->space_order & 1))
+    return fail(WP_EINVAL, "space_order must be even in [2, 16] (got %d)", g->space_order);
+  for (int a = 0; a < g->ndim; ++a) {
+    if (g->shape[a] < 2 || g->shape[a] > (1 << 24))
+      return fail(WP_EINVAL, "shape[%d] = %lld out of range [2, 2^24]", a, (long long)g->shape[a]);
+    if (!(g->spacing[a] > 0) || !std::isfinite(g->spacing[a]))
+      return fail(WP_EINVAL, "spacing[%d] must be positive and finite", a);
+    if (!std::isfinite(g->origin[a])) return fail(WP_EINVAL, "origin[%d] must be finite", a);
+  }
+  if (g->nt < 0) return fail(WP_EINVAL, "nt must be >= 0");
+  if (need_dt && (!(g->dt > 0) || !std::isfinite(g->dt))) return fail(WP_EINVAL, "dt must be positive");
+  G->ndim = g->ndim;
+  G->k = g->space_order;
+  G->R = g->space_order / 2;
+  G->dt = g->dt;
+  G->nt = g->nt;
+  if (g->ndim == 3) {
+    G->nz = int(g->shape[0]);
+    G->ny = int(g->shape[1]);
+    G->nx = int(g->shape[2]);
+    for (int a = 0; a < 3; ++a) {
+      G->h[a] = g->spacing[a];
+      G->o[a] = g->origin[a];
+    }
+  } else {
+    G->nz = int(g->shape[0]);
+    G->ny = 1;
+    G->nx = int(g->shape[1]);
+    G->h[0] = g->spacing[0];
+    G->o[0] = g->origin[0];
+    G->h[1] = 1.0;
+    G->o[1] = 0.0;
+    G->h[2] = g->spacing[1];
+    G->o[2] = g->origin[1];
+  }
+  G->pitch = int(round_up(size_t(G->nx), 32));
+  G->plane = static_cast<long long>(G->ny) * G->pitch;
+  G->nfield = G->plane * G->nz;
+  G->npoints = static_cast<long long>(G->nx) * G->ny * G->nz;
+  if (G->nfield > (1ll << 36)) return fail(WP_EINVAL, "grid too large");
+  G->tiles_x = (G->nx + kTX - 1) / kTX;
+  G->tiles_y = (G->ny + kTY - 1) / kTY;
+  return WP_OK;
+}
+
+static LapCoef lap_coef(const Geom &G) {
+  double a[9];
+  weights(G.k, a);
+  LapCoef c;
+  memset(&c, 0, sizeof c);
+  const double iz = 1.0 / (G.h[0] * G.h[0]), iy = G.ndim == 3 ? 1.0 / (G.h[1] * G.h[1]) : 0.0,
+               ix = 1.0 / (G.h[2] * G.h[2]);
+  c.c0 = static_cast<float>(a[0] * (iz + iy + ix));
+  for (int j = 1; j <= G.R; ++j) {
+    c.cz[j] = static_cast<float>(a[j] * iz);
+    c.cy[j] = static_cast<float>(a[j] * iy);
+    c.cx[j] = static_cast<float>(a[j] * ix);
+  }
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// sparse points: multilinear corners (double precision decisions), pitched
+// ---------------------------------------------------------------------------
+struct PointSet {
+  int npts = 0, nc = 0;
+  std::vector<long long> idx;  // [npts][nc]
+  std::vector<float> w;        // [npts][nc]
+};
+
+static int build_points(const Geom &G, int npts, const double *coords, PointSet *ps, const char *what) {
+  ps->npts = npts;
+  ps->nc = G.ndim == 3 ? 8 : 4;
+  ps->idx.assign(size_t(npts) * ps->nc, 0);
+  ps->w.assign(size_t(npts) * ps->nc, 0.f);
+  if (npts > 0 && !coords) return fail(WP_EINVAL, "%s coordinates are NULL", what);
+  const int axes3[3] = {0, 1, 2}, axes2[2] = {0, 2};
+  const int *axes = G.ndim == 3 ? axes3 : axes2;
+  const int n_of[3] = {G.nz, G.ny, G.nx};
+  for (int i = 0; i < npts; ++i) {
+    long long base[3] = {0, 0, 0};
+    double frac[3] = {0, 0, 0};
+    for (int q = 0; q < G.ndim; ++q) {
+      const int d = axes[q];
+      const double c = coords[size_t(i) * G.ndim + q];
+      if (!std::isfinite(c)) return fail(WP_ENONFINITE, "%s %d has a non-finite coordinate", what, i);
+      double t = (c - G.o[d]) / G.h[d];
+      if (!(t >= -1e-9) || !(t <= double(n_of[d] - 1) + 1e-9))
+        return fail(WP_EINVAL, "%s %d lies outside the grid on axis %d", what, i, q);
+      t = std::min(std::max(t, 0.0), double(n_of[d] - 1));
+      long long b = static_cast<long long>(std::floor(t));
+      if (b > n_of[d] - 2) b = n_of[d] - 2;
+      if (b < 0) b = 0;
+      base[d] = b;
+      frac[d] = t - double(b);
+    }
+    int c = 0;
+    for (int cz = 0; cz < 2; ++cz)
+      for (int cy = 0; cy < (G.ndim == 3 ? 2 : 1); ++cy)
+        for (int cx = 0; cx < 2; ++cx) {
+          double w = (cz ? frac[0] : 1.0 - frac[0]);
+          if (G.ndim == 3) w *= (cy ? frac[1] : 1.0 - frac[1]);
+          w *= (cx ? frac[2] : 1.0 - frac[2]);
+          const long long z = base[0] + cz, y = base[1] + cy, x = base[2] + cx;
+          ps->idx[size_t(i) * ps->nc + c] = z * G.plane + y * G.pitch + x;
+          ps->w[size_t(i) * ps->nc + c] = static_cast<float>(w);
+          ++c;
+        }
+  }
+  return WP_OK;
+}
+
+// Device copy of a point set: gather form (interpolation) and CSR scatter form
+// (injection, entries of one target in (point, corner) order).
+struct DevPoints {
+  int npts = 0, nc = 0, ntarget = 0;
+  long long *idx = nullptr;
+  float *w = nullptr;
+  long long *target = nullptr;
+  int *rowptr = nullptr;
+  int *pid = nullptr;
+  float *cw = nullptr;
+};
+
+static int upload_points(wp_ctx *c, Arena &ar, const PointSet &ps, bool gather, bool scatter, DevPoints *dp) {
+  dp->npts = ps.npts;
+  dp->nc = ps.nc;
+  if (ps.npts == 0) return WP_OK;
+  const size_t ne = size_t(ps.npts) * ps.nc;
+  if (gather) {
+    TRY(ar.alloc(&dp->idx, ne));
+    TRY(ar.alloc(&dp->w, ne));
+    CU(cudaMemcpyAsync(dp->idx, ps.idx.data(), ne * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(dp->w, ps.w.data(), ne * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  }
+  if (scatter) {
+    std::vector<size_t> order(ne);
+    for (size_t e = 0; e < ne; ++e) order[e] = e;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return ps.idx[a] < ps.idx[b]; });
+    std::vector<long long> target;
+    std::vector<int> rowptr, pid;
+    std::vector<float> cw;
+    for (size_t k = 0; k < ne; ++k) {
+      const size_t e = order[k];
+      if (target.empty() || target.back() != ps.idx[e]) {
+        target.push_back(ps.idx[e]);
+        rowptr.push_back(int(k));
+      }
+      pid.push_back(int(e / ps.nc));
+      cw.push_back(ps.w[e]);
+    }
+    rowptr.push_back(int(ne));
+    dp->ntarget = int(target.size());
+    TRY(ar.alloc(&dp->target, target.size()));
+    TRY(ar.alloc(&dp->rowptr, rowptr.size()));
+    TRY(ar.alloc(&dp->pid, pid.size()));
+    TRY(ar.alloc(&dp->cw, cw.size()));
+    // pageable sources: these copies complete before returning, so the vectors may go
+    CU(cudaMemcpy(dp->target, target.data(), target.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(dp->rowptr, rowptr.data(), rowptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(dp->pid, pid.data(), pid.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(dp->cw, cw.data(), cw.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  return WP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// TMA descriptors
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static int get_encode() {
+  if (g_encode) return WP_OK;
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+    return fail(WP_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return WP_OK;
+}
+
+// 3D map over a pitched field, box (bx, by, 1); out-of-range elements read as 0.
+static int make_map(CUtensorMap *m, const float *base, const Geom &G, int bx, int by) {
+  cuuint64_t dims[3] = {cuuint64_t(G.nx), cuuint64_t(G.ny), cuuint64_t(G.nz)};
+  cuuint64_t strides[2] = {cuuint64_t(G.pitch) * 4, cuuint64_t(G.plane) * 4};
+  cuuint32_t box[3] = {cuuint32_t(bx), cuuint32_t(by), 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(WP_ECUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
+  return WP_OK;
+}
+
+static int halo_box_w(int R) { return kTX + 2 * ((R + 3) / 4 * 4); }
+
+// A field and its two descriptors (halo'd plane box, tile box).
+struct Field3 {
+  float *p = nullptr;
+  CUtensorMap halo, tile;
+};
+
+static int make_field_maps(Field3 *f, const Geom &G) {
+  if (G.ndim != 3) return WP_OK;
+  TRY(make_map(&f->halo, f->p, G, halo_box_w(G.R), kTY + 2 * G.R));
+  TRY(make_map(&f->tile, f->p, G, kTX, kTY));
+  return WP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the propagator of one call: coefficients, launch configuration, step launches
+// ---------------------------------------------------------------------------
+struct Prop {
+  wp_ctx *c = nullptr;
+  Geom G;
+  LapCoef lc;
+  float neg_inv_dt2 = 0;
+  Field3 b, s;
+  unsigned char *tflag = nullptr;
+  dim3 grid3;
+  int zchunk = 0;
+};
+
+static int prop_setup(wp_ctx *c, Arena &ar, const Geom &G, const float *m, const float *eta, Prop *P) {
+  P->c = c;
+  P->G = G;
+  P->lc = lap_coef(G);
+  P->neg_inv_dt2 = static_cast<float>(-1.0 / (G.dt * G.dt));
+  TRY(ar.alloc(&P->b.p, G.nfield));
+  TRY(ar.alloc(&P->s.p, G.nfield));
+  CU(cudaMemsetAsync(c->d_scalars, 0, 4 * sizeof(int), c->stream));
+  CoefArgs a;
+  memset(&a, 0, sizeof a);
+  a.m = m;
+  a.eta = eta;
+  a.g = G.fg();
+  a.dt = G.dt;
+  a.b = P->b.p;
+  a.s = P->s.p;
+  if (G.ndim == 3) {
+    const size_t nflag = size_t(G.nz) * G.tiles_y * G.tiles_x;
+    TRY(ar.alloc(&P->tflag, nflag));
+    CU(cudaMemsetAsync(P->tflag, 0, nflag, c->stream));
+    a.tflag = P->tflag;
+    a.tiles_x = G.tiles_x;
+    a.tiles_y = G.tiles_y;
+    a.tile_w = kTX;
+    a.tile_h = kTY;
+  }
+  a.max_inv_m_bits = reinterpret_cast<unsigned int *>(c->d_scalars + 2);
+  a.bad = c->d_scalars + 1;
+  CU(launch_coef(c->stream, a));
+  c->launches++;
+  CU(cudaMemcpyAsync(c->h_scalars, c->d_scalars, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  TRY(ctx_wait(c));
+  if (c->h_scalars[1] & 1) return fail(WP_ENONFINITE, "m or eta holds NaN or Inf");
+  if (c->h_scalars[1] & 2) return fail(WP_EINVAL, "m must be > 0 and eta >= 0 everywhere");
+  float max_inv_m;
+  memcpy(&max_inv_m, &c->h_scalars[2], 4);
+  const double vmax = std::sqrt(double(max_inv_m));
+  const double lim = cfl_limit(G, vmax);
+  if (G.dt > lim * (1.0 + 1e-5))
+    return fail(WP_ECFL, "dt = %.6g exceeds the stability limit %.6g for vmax = %.6g", G.dt, lim, vmax);
+  if (G.ndim == 3) {
+    TRY(get_encode());
+    TRY(make_field_maps(&P->b, G));
+    TRY(make_field_maps(&P->s, G));
+    const int ntile = G.tiles_x * G.tiles_y;
+    const int slots = c->num_sms * std::max(1, c->occ3d[0][G.R]);
+    int nchunk = std::max(1, slots / ntile);
+    const char *env = getenv("WP_ZCHUNK");
+    int zc = (G.nz + nchunk - 1) / nchunk;
+    if (env && atoi(env) > 0) zc = atoi(env);
+    zc = std::max(zc, std::min(G.nz, 8));
+    P->zchunk = zc;
+    P->grid3 = dim3(G.tiles_x, G.tiles_y, (G.nz + zc - 1) / zc);
+  }
+  return WP_OK;
+}
+
+// One stencil step: out = update(u, um) (out may alias um).  Adjoint+gradient
+// mode also accumulates into grad using the forward field uj.
+static int prof_mark(wp_ctx *c) {
+  if (!c->profiling) return WP_OK;
+  if (c->prof_used == c->prof_events.size()) {
+    cudaEvent_t e;
+    CU(cudaEventCreate(&e));
+    c->prof_events.push_back(e);
+  }
+  CU(cudaEventRecord(c->prof_events[c->prof_used++], c->stream));
+  return WP_OK;
+}
+
+// Fold the recorded stencil intervals into the totals (the stream must be idle).
+static int prof_collect(wp_ctx *c) {
+  for (size_t i = 0; i + 1 < c->prof_used; i += 2) {
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, c->prof_events[i], c->prof_events[i + 1]));
+    c->prof_ms += ms;
+    c->prof_count++;
+  }
+  c->prof_used = 0;
+  return WP_OK;
+}
+
+static int prop_step(Prop &P, const Field3 &u, const Field3 &um, float *out, int mode, const Field3 *uj,
+                     const Field3 *grad) {
+  const Geom &G = P.G;
+  TRY(prof_mark(P.c));
+  if (G.ndim == 3) {
+    Stencil3dArgs a;
+    a.g = G.fg();
+    a.c = P.lc;
+    a.u = u.p;
+    a.out = out;
+    a.grad = grad ? grad->p : nullptr;
+    a.neg_inv_dt2 = P.neg_inv_dt2;
+    a.tflag = P.tflag;
+    a.tiles_x = G.tiles_x;
+    a.tiles_y = G.tiles_y;
+    a.zchunk = P.zchunk;
+    a.err = P.c->d_scalars;
+    CUtensorMap maps[6] = {u.halo, um.tile, P.b.tile, P.s.tile, uj ? uj->tile : P.b.tile,
+                           grad ? grad->tile : P.b.tile};
+    cudaError_t e = mode == kModeAdjGrad ? launch_stencil3d_adj(G.R, P.grid3, P.c->stream, maps, a)
+                                         : launch_stencil3d_fwd(G.R, P.grid3, P.c->stream, maps, a);
+    if (e != cudaSuccess) return fail(WP_ECUDA, "stencil3d launch failed: %s", cudaGetErrorString(e));
+  } else {
+    Stencil2dArgs a;
+    a.g = G.fg();
+    a.c = P.lc;
+    a.u = u.p;
+    a.um = um.p;
+    a.b = P.b.p;
+    a.s = P.s.p;
+    a.out = out;
+    a.grad = grad ? grad->p : nullptr;
+    a.uj = uj ? uj->p : nullptr;
+    a.neg_inv_dt2 = P.neg_inv_dt2;
+    cudaError_t e = launch_stencil2d(G.R, mode, P.c->stream, a);
+    if (e != cudaSuccess) return fail(WP_ECUDA, "stencil2d launch failed: %s", cudaGetErrorString(e));
+  }
+  P.c->launches++;
+  TRY(prof_mark(P.c));
+  if (P.c->prof_used >= 4096) {  // bound the event pool: fold what has completed
+    TRY(ctx_wait(P.c));
+    TRY(prof_collect(P.c));
+  }
+  return WP_OK;
+}
+
+static int prop_inject(Prop &P, const DevPoints &dp, const float *data, long long row, float *u, float *grad,
+                       const float *uj) {
+  if (dp.ntarget == 0) return WP_OK;
+  InjectArgs a;
+  a.ntarget = dp.ntarget;
+  a.target = dp.target;
+  a.rowptr = dp.rowptr;
+  a.pid = dp.pid;
+  a.w = dp.cw;
+  a.data = data;
+  a.npts = dp.npts;
+  a.row = row;
+  a.u = u;
+  a.b = P.b.p;
+  a.grad = grad;
+  a.uj = uj;
+  a.neg_inv_dt2 = P.neg_inv_dt2;
+  CU(launch_inject(P.c->stream, a));
+  P.c->launches++;
+  return WP_OK;
+}
+
+static int prop_sample(Prop &P, const DevPoints &dp, const float *u, float *out, long long row) {
+  if (dp.npts == 0) return WP_OK;
+  InterpArgs a;
+  a.npts = dp.npts;
+  a.ncorner = dp.nc;
+  a.idx = dp.idx;
+  a.w = dp.w;
+  a.u = u;
+  a.out = out;
+  a.row = row;
+  CU(launch_interp(P.c->stream, a));
+  P.c->launches++;
+  return WP_OK;
+}
+
+static int alloc_field(Arena &ar, const Geom &G, Field3 *f, bool zero, cudaStream_t st) {
+  TRY(ar.alloc(&f->p, G.nfield));
+  if (zero) CU(cudaMemsetAsync(f->p, 0, G.field_bytes(), st));
+  TRY(make_field_maps(f, G));
+  return WP_OK;
+}
+
+// Time loop shared by forward and adjoint: for k = 0..nt-1 one update, inject
+// data row (dir > 0 ? k : nt-1-k) at `inj`, sample `smp` into the same row of
+// `out`.  u[k & 1] holds the current level before step k.
+static int run_loop(Prop &P, Field3 u[2], int nt, const DevPoints &inj, const float *data, const DevPoints &smp,
+                    float *out, int dir) {
+  for (int k = 0; k < nt; ++k) {
+    const long long row = dir > 0 ? k : nt - 1 - k;
+    Field3 &cur = u[k & 1], &prv = u[(k + 1) & 1];
+    TRY(prop_step(P, cur, prv, prv.p, kModeFwd, nullptr, nullptr));
+    TRY(prop_inject(P, inj, data, row, prv.p, nullptr, nullptr));
+    if (out) TRY(prop_sample(P, smp, prv.p, out, row));
+  }
+  return WP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// common call prologue
+// ---------------------------------------------------------------------------
+static int enter(wp_ctx *c, void *user_stream) {
+  if (!c) return fail(WP_EINVAL, "context is NULL");
+  if (c->broken) return fail(WP_ETIMEOUT, "context unusable after an earlier timeout");
+  CU(cudaSetDevice(c->device));
+  cudaStream_t us = static_cast<cudaStream_t>(user_stream);
+  CU(cudaEventRecord(c->ev_in, us));
+  CU(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+  CU(cudaMemsetAsync(c->d_scalars, 0, 4 * sizeof(int), c->stream));
+  return WP_OK;
+}
+
+static int leave(wp_ctx *c, void *user_stream, int rc) {
+  if (rc == WP_OK) rc = check_device_error(c);
+  if (rc == WP_OK && c->profiling) rc = prof_collect(c);
+  if (rc != WP_OK && c) c->prof_used = 0;
+  if (rc != WP_ETIMEOUT && c && !c->broken) {
+    // order the caller's later work after ours (normally complete already)
+    if (cudaEventRecord(c->ev_done, c->stream) == cudaSuccess)
+      cudaStreamWaitEvent(static_cast<cudaStream_t>(user_stream), c->ev_done, 0);
+    if (rc != WP_OK) cudaStreamSynchronize(c->stream);
+  }
+  return rc;
+}
+
+static bool all_finite(const float *x, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(x[i])) return false;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// forward / adjoint
+// ---------------------------------------------------------------------------
+// host_io: inputs/outputs are host pointers (copied in/out); otherwise device.
+static int do_propagate(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *inj_data,
+                        int ninj, const double *inj_xyz, int nsmp, const double *smp_xyz, float *smp_out, int dir,
+                        bool host_io) {
+  Geom G;
+  TRY(make_geom(grid, &G));
+  if (ninj < 0 || nsmp < 0) return fail(WP_EINVAL, "point counts must be >= 0");
+  if (!m || !eta) return fail(WP_EINVAL, "m and eta must not be NULL");
+  if (ninj > 0 && G.nt > 0 && !inj_data) return fail(WP_EINVAL, "injected data is NULL");
+  if (nsmp > 0 && G.nt > 0 && !smp_out) return fail(WP_EINVAL, "output array is NULL");
+  PointSet pin, psm;
+  TRY(build_points(G, ninj, inj_xyz, &pin, dir > 0 ? "source" : "receiver"));
+  TRY(build_points(G, nsmp, smp_xyz, &psm, dir > 0 ? "receiver" : "source"));
+  const size_t n_in = size_t(G.nt) * ninj, n_out = size_t(G.nt) * nsmp;
+  if (host_io && n_in && !all_finite(inj_data, n_in)) return fail(WP_ENONFINITE, "injected data holds NaN or Inf");
+
+  Arena ar(c);
+  Field3 u[2];
+  TRY(alloc_field(ar, G, &u[0], false, c->stream));
+  TRY(alloc_field(ar, G, &u[1], false, c->stream));
+  const float *md = m, *ed = eta;
+  if (host_io) {  // stage m, eta contiguously in the wavefield buffers
+    CU(cudaMemcpyAsync(u[0].p, m, G.npoints * 4, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(u[1].p, eta, G.npoints * 4, cudaMemcpyHostToDevice, c->stream));
+    md = u[0].p;
+    ed = u[1].p;
+  }
+  Prop P;
+  TRY(prop_setup(c, ar, G, md, ed, &P));
+  CU(cudaMemsetAsync(u[0].p, 0, G.field_bytes(), c->stream));
+  CU(cudaMemsetAsync(u[1].p, 0, G.field_bytes(), c->stream));
+  DevPoints din, dsm;
+  TRY(upload_points(c, ar, pin, false, true, &din));
+  TRY(upload_points(c, ar, psm, true, false, &dsm));
+  const float *data_d = inj_data;
+  float *out_d = smp_out;
+  if (host_io) {
+    float *tmp_in = nullptr, *tmp_out = nullptr;
+    if (n_in) {
+      TRY(ar.alloc(&tmp_in, n_in));
+      CU(cudaMemcpyAsync(tmp_in, inj_data, n_in * 4, cudaMemcpyHostToDevice, c->stream));
+    }
+    if (n_out) TRY(ar.alloc(&tmp_out, n_out));
+    data_d = tmp_in;
+    out_d = tmp_out;
+  } else if (n_in) {
+    int *bad = c->d_scalars + 1;
+    CU(cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+    CU(launch_check_finite(c->stream, inj_data, (long long)n_in, bad));
+    c->launches++;
+    CU(cudaMemcpyAsync(c->h_scalars + 1, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    TRY(ctx_wait(c));
+    if (c->h_scalars[1]) return fail(WP_ENONFINITE, "injected data holds NaN or Inf");
+  }
+  TRY(run_loop(P, u, G.nt, din, data_d, dsm, n_out ? out_d : nullptr, dir));
+  if (host_io && n_out) CU(cudaMemcpyAsync(smp_out, out_d, n_out * 4, cudaMemcpyDeviceToHost, c->stream));
+  return ctx_wait(c);
+}
+
+// ---------------------------------------------------------------------------
+// gradient: forward with snapshots, backward with recompute + fused gradient
+// ---------------------------------------------------------------------------
+struct wp_state {
+  wp_ctx *c = nullptr;
+  Geom G;
+  Prop P;
+  std::vector<void *> mem;     // device blocks owned by the state
+  float *snaps = nullptr;      // [nseg][2][nfield]: (u^{sS-1}, u^{sS})
+  int S = 0, nseg = 0;
+  PointSet psrc, prec;
+  DevPoints dsrc, drec;
+  float *wavelet = nullptr;    // [nt][nsrc] device copy
+};
+
+static void state_release(wp_state *st) {
+  if (!st) return;
+  for (void *p : st->mem) dev_free(st->c, p);
+  st->mem.clear();
+}
+
+static int forward_save(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *wavelet,
+                        int nsrc, const double *src_xyz, int nrec, const double *rec_xyz, int snap_interval,
+                        float *rec_out, bool host_io, wp_state **out) {
+  *out = nullptr;
+  wp_state *st = new wp_state();
+  st->c = c;
+  int rc = [&]() -> int {
+    Geom &G = st->G;
+    TRY(make_geom(grid, &G));
+    if (nsrc < 0 || nrec < 0) return fail(WP_EINVAL, "point counts must be >= 0");
+    if (!m || !eta) return fail(WP_EINVAL, "m and eta must not be NULL");
+    if (nsrc > 0 && G.nt > 0 && !wavelet) return fail(WP_EINVAL, "wavelet is NULL");
+    if (snap_interval < 1) return fail(WP_EINVAL, "snap_interval must be >= 1");
+    st->S = snap_interval;
+    st->nseg = (G.nt + st->S - 1) / st->S;
+    TRY(build_points(G, nsrc, src_xyz, &st->psrc, "source"));
+    TRY(build_points(G, nrec, rec_xyz, &st->prec, "receiver"));
+    const size_t n_in = size_t(G.nt) * nsrc, n_out = size_t(G.nt) * nrec;
+    if (host_io && n_in && !all_finite(wavelet, n_in)) return fail(WP_ENONFINITE, "wavelet holds NaN or Inf");
+    Arena keep(c);   // memory owned by the state
+    Arena tmp(c);    // memory of this call only
+    Field3 u[2];
+    TRY(alloc_field(tmp, G, &u[0], false, c->stream));
+    TRY(alloc_field(tmp, G, &u[1], false, c->stream));
+    const float *md = m, *ed = eta;
+    if (host_io) {
+      CU(cudaMemcpyAsync(u[0].p, m, G.npoints * 4, cudaMemcpyHostToDevice, c->stream));
+      CU(cudaMemcpyAsync(u[1].p, eta, G.npoints * 4, cudaMemcpyHostToDevice, c->stream));
+      md = u[0].p;
+      ed = u[1].p;
+    }
+    TRY(prop_setup(c, keep, G, md, ed, &st->P));
+    CU(cudaMemsetAsync(u[0].p, 0, G.field_bytes(), c->stream));
+    CU(cudaMemsetAsync(u[1].p, 0, G.field_bytes(), c->stream));
+    TRY(upload_points(c, keep, st->psrc, false, true, &st->dsrc));
+    TRY(upload_points(c, keep, st->prec, true, true, &st->drec));
+    if (n_in) {
+      TRY(keep.alloc(&st->wavelet, n_in));
+      CU(cudaMemcpyAsync(st->wavelet, wavelet, n_in * 4, host_io ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                         c->stream));
+      if (!host_io) {
+        int *bad = c->d_scalars + 1;
+        CU(cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+        CU(launch_check_finite(c->stream, st->wavelet, (long long)n_in, bad));
+        c->launches++;
+        CU(cudaMemcpyAsync(c->h_scalars + 1, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        TRY(ctx_wait(c));
+        if (c->h_scalars[1]) return fail(WP_ENONFINITE, "wavelet holds NaN or Inf");
+      }
+    }
+    if (st->nseg > 0) TRY(keep.alloc(&st->snaps, size_t(st->nseg) * 2 * G.nfield));
+    float *rec_d = nullptr;
+    if (rec_out && n_out) {
+      if (host_io) TRY(tmp.alloc(&rec_d, n_out));
+      else rec_d = rec_out;
+    }
+    Prop &P = st->P;
+    for (int n = 0; n < G.nt; ++n) {
+      Field3 &cur = u[n & 1], &prv = u[(n + 1) & 1];
+      if (n % st->S == 0) {
+        float *dst = st->snaps + size_t(n / st->S) * 2 * G.nfield;
+        CU(cudaMemcpyAsync(dst, prv.p, G.field_bytes(), cudaMemcpyDeviceToDevice, c->stream));
+        CU(cudaMemcpyAsync(dst + G.nfield, cur.p, G.field_bytes(), cudaMemcpyDeviceToDevice, c->stream));
+      }
+      TRY(prop_step(P, cur, prv, prv.p, kModeFwd, nullptr, nullptr));
+      TRY(prop_inject(P, st->dsrc, st->wavelet, n, prv.p, nullptr, nullptr));
+      if (rec_d) TRY(prop_sample(P, st->drec, prv.p, rec_d, n));
+    }
+    if (host_io && rec_d) CU(cudaMemcpyAsync(rec_out, rec_d, n_out * 4, cudaMemcpyDeviceToHost, c->stream));
+    TRY(ctx_wait(c));
+    keep.release_all_to(st->mem);
+    return WP_OK;
+  }();
+  if (rc != WP_OK) {
+    state_release(st);
+    delete st;
+    return rc;
+  }
+  *out = st;
+  return WP_OK;
+}
+
+static int backward(wp_state *st, const float *residual, float *grad_out, bool host_io) {
+  wp_ctx *c = st->c;
+  const Geom &G = st->G;
+  Prop &P = st->P;
+  const int nrec = st->drec.npts;
+  const size_t n_res = size_t(G.nt) * nrec;
+  if (n_res && !residual) return fail(WP_EINVAL, "residual is NULL");
+  if (!grad_out) return fail(WP_EINVAL, "grad_out is NULL");
+  if (host_io && n_res && !all_finite(residual, n_res)) return fail(WP_ENONFINITE, "residual holds NaN or Inf");
+  Arena tmp(c);
+  const float *res_d = residual;
+  if (n_res) {
+    float *r = nullptr;
+    if (host_io) {
+      TRY(tmp.alloc(&r, n_res));
+      CU(cudaMemcpyAsync(r, residual, n_res * 4, cudaMemcpyHostToDevice, c->stream));
+      res_d = r;
+    } else {
+      int *bad = c->d_scalars + 1;
+      CU(cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+      CU(launch_check_finite(c->stream, residual, (long long)n_res, bad));
+      c->launches++;
+      CU(cudaMemcpyAsync(c->h_scalars + 1, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+      TRY(ctx_wait(c));
+      if (c->h_scalars[1]) return fail(WP_ENONFINITE, "residual holds NaN or Inf");
+    }
+  }
+  const int S = st->S;
+  std::vector<Field3> ring(size_t(std::min(S, std::max(G.nt, 1))) + 2);
+  for (auto &f : ring) TRY(alloc_field(tmp, G, &f, false, c->stream));
+  Field3 w[2], g;
+  TRY(alloc_field(tmp, G, &w[0], true, c->stream));
+  TRY(alloc_field(tmp, G, &w[1], true, c->stream));
+  TRY(alloc_field(tmp, G, &g, true, c->stream));
+  long long kadj = 0;  // adjoint steps done: w^{j+1} in w[kadj & 1]
+  for (int s = st->nseg - 1; s >= 0; --s) {
+    const int s0 = s * S;
+    const int len = std::min(S, G.nt - s0);
+    const float *snap = st->snaps + size_t(s) * 2 * G.nfield;
+    CU(cudaMemcpyAsync(ring[0].p, snap, G.field_bytes(), cudaMemcpyDeviceToDevice, c->stream));
+    CU(cudaMemcpyAsync(ring[1].p, snap + G.nfield, G.field_bytes(), cudaMemcpyDeviceToDevice, c->stream));
+    for (int i = 0; i < len; ++i) {  // recompute u^{s0+1} .. u^{s0+len} into ring[2..]
+      TRY(prop_step(P, ring[i + 1], ring[i], ring[i + 2].p, kModeFwd, nullptr, nullptr));
+      TRY(prop_inject(P, st->dsrc, st->wavelet, s0 + i, ring[i + 2].p, nullptr, nullptr));
+    }
+    for (int j = s0 + len; j >= s0 + 1; --j, ++kadj) {
+      Field3 &w1 = w[kadj & 1], &w2 = w[(kadj + 1) & 1];
+      const Field3 &uj = ring[j - s0 + 1];
+      TRY(prop_step(P, w1, w2, w2.p, kModeAdjGrad, &uj, &g));
+      TRY(prop_inject(P, st->drec, res_d, j - 1, w2.p, g.p, uj.p));
+    }
+  }
+  // pitched -> contiguous
+  CU(cudaMemcpy2DAsync(grad_out, size_t(G.nx) * 4, g.p, size_t(G.pitch) * 4, size_t(G.nx) * 4,
+                       size_t(G.ny) * G.nz, host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
+  return ctx_wait(c);
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *wp_last_error(void) { return g_err.c_str(); }
+
+int wp_create(wp_ctx **out, int device, size_t budget) {
+  if (!out) return fail(WP_EINVAL, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  CU(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(WP_EINVAL, "device %d not present (%d devices)", device, ndev);
+  CU(cudaSetDevice(device));
+  wp_ctx *c = new wp_ctx();
+  c->device = device;
+  int rc = [&]() -> int {
+    CU(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+    size_t fr = 0, tot = 0;
+    CU(cudaMemGetInfo(&fr, &tot));
+    c->budget = budget == WP_BUDGET_AUTO ? size_t(0.9 * double(fr)) : budget;
+    CU(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming));
+    CU(cudaMalloc(&c->d_scalars, 64));
+    CU(cudaMallocHost(&c->h_scalars, 64));
+    CU(cudaMemset(c->d_scalars, 0, 64));
+    for (int R = 1; R <= 8; ++R) {
+      CU(prepare_stencil3d_fwd(R, &c->smem3d[0][R], &c->occ3d[0][R]));
+      CU(prepare_stencil3d_adj(R, &c->smem3d[1][R], &c->occ3d[1][R]));
+    }
+    return WP_OK;
+  }();
+  if (rc != WP_OK) {
+    wp_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return WP_OK;
+}
+
+void wp_destroy(wp_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream && !c->broken) cudaStreamSynchronize(c->stream);
+  for (auto &kv : c->live) cudaFree(kv.first);
+  for (auto &kv : c->cache) cudaFree(kv.second);
+  if (c->d_scalars) cudaFree(c->d_scalars);
+  if (c->h_scalars) cudaFreeHost(c->h_scalars);
+  for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_done) cudaEventDestroy(c->ev_done);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+int wp_set_timeout(wp_ctx *c, double seconds) {
+  if (!c || !(seconds > 0)) return fail(WP_EINVAL, "bad context or timeout");
+  c->timeout_s = seconds;
+  return WP_OK;
+}
+
+size_t wp_bytes_in_use(const wp_ctx *c) { return c ? c->in_use : 0; }
+
+int wp_set_profiling(wp_ctx *c, int enabled) {
+  if (!c) return fail(WP_EINVAL, "context is NULL");
+  c->profiling = enabled != 0;
+  c->prof_used = 0;
+  return WP_OK;
+}
+
+int wp_profile_read(wp_ctx *c, double *stencil_ms, uint64_t *stencil_launches, int reset) {
+  if (!c) return fail(WP_EINVAL, "context is NULL");
+  if (stencil_ms) *stencil_ms = c->prof_ms;
+  if (stencil_launches) *stencil_launches = c->prof_count;
+  if (reset) {
+    c->prof_ms = 0.0;
+    c->prof_count = 0;
+  }
+  return WP_OK;
+}
+uint64_t wp_kernel_launches(const wp_ctx *c) { return c ? c->launches : 0; }
+
+int wp_fd_weights(int k, double *alpha) {
+  if (!alpha) return fail(WP_EINVAL, "alpha is NULL");
+  if (!weights(k, alpha)) return fail(WP_EINVAL, "space_order must be even in [2, 16] (got %d)", k);
+  return WP_OK;
+}
+
+int wp_cfl_dt(const wp_grid *grid, double vmax, double *dt_max) {
+  Geom G;
+  TRY(make_geom(grid, &G, false));
+  if (!dt_max) return fail(WP_EINVAL, "dt_max is NULL");
+  if (!(vmax > 0) || !std::isfinite(vmax)) return fail(WP_EINVAL, "vmax must be positive");
+  *dt_max = cfl_limit(G, vmax);
+  return WP_OK;
+}
+
+int wp_estimate_bytes(const wp_grid *grid, int nsrc, int nrec, int mode, int snap_interval, size_t *bytes) {
+  Geom G;
+  TRY(make_geom(grid, &G, false));
+  if (!bytes) return fail(WP_EINVAL, "bytes is NULL");
+  const size_t f = round_up(G.field_bytes(), 256);
+  const size_t pts = size_t(nsrc + nrec) * 8 * 24 + size_t(G.nt) * (nsrc + nrec) * 4 * 2;
+  const size_t flags = size_t(G.nz) * G.tiles_x * G.tiles_y;
+  size_t b = 4 * f + pts + flags + (1 << 20);
+  if (mode == 1) {
+    const int S = std::max(snap_interval, 1);
+    const size_t nseg = (size_t(G.nt) + S - 1) / S;
+    b += 2 * nseg * f + size_t(std::min(S, std::max(G.nt, 1)) + 2 + 3) * f;
+  }
+  *bytes = b;
+  return WP_OK;
+}
+
+int wp_forward_dev(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *wavelet, int nsrc,
+                   const double *src, int nrec, const double *rec, float *rec_out, void *stream) {
+  TRY(enter(c, stream));
+  return leave(c, stream, do_propagate(c, grid, m, eta, wavelet, nsrc, src, nrec, rec, rec_out, +1, false));
+}
+
+int wp_forward(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *wavelet, int nsrc,
+               const double *src, int nrec, const double *rec, float *rec_out) {
+  TRY(enter(c, nullptr));
+  return leave(c, nullptr, do_propagate(c, grid, m, eta, wavelet, nsrc, src, nrec, rec, rec_out, +1, true));
+}
+
+int wp_adjoint_dev(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *rec_data, int nrec,
+                   const double *rec, int nsrc, const double *src, float *src_out, void *stream) {
+  TRY(enter(c, stream));
+  return leave(c, stream, do_propagate(c, grid, m, eta, rec_data, nrec, rec, nsrc, src, src_out, -1, false));
+}
+
+int wp_adjoint(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *rec_data, int nrec,
+               const double *rec, int nsrc, const double *src, float *src_out) {
+  TRY(enter(c, nullptr));
+  return leave(c, nullptr, do_propagate(c, grid, m, eta, rec_data, nrec, rec, nsrc, src, src_out, -1, true));
+}
+
+static int gradient_impl(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *wavelet,
+                         int nsrc, const double *src, const float *residual, int nrec, const double *rec, int S,
+                         float *grad_out, bool host_io) {
+  wp_state *st = nullptr;
+  TRY(forward_save(c, grid, m, eta, wavelet, nsrc, src, nrec, rec, S, nullptr, host_io, &st));
+  int rc = backward(st, residual, grad_out, host_io);
+  state_release(st);
+  delete st;
+  return rc;
+}
+
+int wp_gradient(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *wavelet, int nsrc,
+                const double *src, const float *residual, int nrec, const double *rec, int S, float *grad_out) {
+  TRY(enter(c, nullptr));
+  return leave(c, nullptr, gradient_impl(c, grid, m, eta, wavelet, nsrc, src, residual, nrec, rec, S, grad_out, true));
+}
+
+int wp_gradient_dev(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *wavelet, int nsrc,
+                    const double *src, const float *residual, int nrec, const double *rec, int S, float *grad_out,
+                    void *stream) {
+  TRY(enter(c, stream));
+  return leave(c, stream,
+               gradient_impl(c, grid, m, eta, wavelet, nsrc, src, residual, nrec, rec, S, grad_out, false));
+}
+
+int wp_forward_save(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *wavelet, int nsrc,
+                    const double *src, int nrec, const double *rec, int S, float *rec_out, void *stream,
+                    wp_state **state) {
+  if (!state) return fail(WP_EINVAL, "state is NULL");
+  *state = nullptr;
+  TRY(enter(c, stream));
+  return leave(c, stream, forward_save(c, grid, m, eta, wavelet, nsrc, src, nrec, rec, S, rec_out, false, state));
+}
+
+int wp_backward(wp_state *st, const float *residual, float *grad_out, void *stream) {
+  if (!st) return fail(WP_EINVAL, "state is NULL");
+  TRY(enter(st->c, stream));
+  return leave(st->c, stream, backward(st, residual, grad_out, false));
+}
+
+void wp_state_free(wp_state *st) {
+  if (!st) return;
+  state_release(st);
+  delete st;
+}
+
+int wp_propagate_dev(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, float *u_prev, float *u,
+                     int nsteps, void *stream) {
+  TRY(enter(c, stream));
+  int rc = [&]() -> int {
+    Geom G;
+    TRY(make_geom(grid, &G));
+    if (!m || !eta || !u_prev || !u) return fail(WP_EINVAL, "NULL field");
+    if (nsteps < 0) return fail(WP_EINVAL, "nsteps must be >= 0");
+    Arena ar(c);
+    Field3 f[2];
+    TRY(alloc_field(ar, G, &f[0], true, c->stream));
+    TRY(alloc_field(ar, G, &f[1], true, c->stream));
+    Prop P;
+    TRY(prop_setup(c, ar, G, m, eta, &P));
+    const size_t w = size_t(G.nx) * 4, hp = size_t(G.pitch) * 4, rows = size_t(G.ny) * G.nz;
+    CU(cudaMemcpy2DAsync(f[0].p, hp, u, w, w, rows, cudaMemcpyDeviceToDevice, c->stream));
+    CU(cudaMemcpy2DAsync(f[1].p, hp, u_prev, w, w, rows, cudaMemcpyDeviceToDevice, c->stream));
+    DevPoints none;
+    TRY(run_loop(P, f, nsteps, none, nullptr, none, nullptr, +1));
+    CU(cudaMemcpy2DAsync(u, w, f[nsteps & 1].p, hp, w, rows, cudaMemcpyDeviceToDevice, c->stream));
+    CU(cudaMemcpy2DAsync(u_prev, w, f[(nsteps + 1) & 1].p, hp, w, rows, cudaMemcpyDeviceToDevice, c->stream));
+    return ctx_wait(c);
+  }();
+  return leave(c, stream, rc);
+}
+
+}  // extern "C"

@@ -1,0 +1,185 @@
+// 2D stencil (K1 in 2D), coefficient setup (A1), injection (K2), interpolation
+// (K3) and input checks.
+#include <math.h>
+
+#include "kernels.cuh"
+#include "stencil3d.cuh"
+
+namespace wp {
+
+// ---------------------------------------------------------------------------
+// K1, 2D: same update as the 3D kernel (see stencil3d.cuh) on (nz, nx) fields.
+// A 32 x 16 output tile per CTA; the halo'd tile of u^n is staged in shared
+// memory with zero values outside the grid; each thread computes two points.
+// ---------------------------------------------------------------------------
+template <int R, int MODE>
+__global__ void __launch_bounds__(256) stencil2d_kernel(const Stencil2dArgs a) {
+  constexpr int TW = 32, TH = 16, SW = TW + 2 * R, SH = TH + 2 * R;
+  __shared__ float tile[SH][SW];
+  const int x0 = blockIdx.x * TW, z0 = blockIdx.y * TH;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const int nx = a.g.nx, nz = a.g.nz, pitch = a.g.pitch;
+  for (int i = tid; i < SH * SW; i += 256) {
+    const int lz = i / SW, lx = i % SW;
+    const int gz = z0 - R + lz, gx = x0 - R + lx;
+    tile[lz][lx] = (gz >= 0 && gz < nz && gx >= 0 && gx < nx)
+                       ? __ldg(a.u + static_cast<long long>(gz) * pitch + gx)
+                       : 0.f;
+  }
+  __syncthreads();
+  const int lx = threadIdx.x + R;
+  const int gx = x0 + threadIdx.x;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int lz = threadIdx.y + 8 * r + R;
+    const int gz = z0 + threadIdx.y + 8 * r;
+    if (gx >= nx || gz >= nz) continue;
+    const float c = tile[lz][lx];
+    float lap = a.c.c0 * c;
+#pragma unroll
+    for (int j = 1; j <= R; ++j) {
+      lap = fmaf(a.c.cx[j], tile[lz][lx + j] + tile[lz][lx - j], lap);
+      lap = fmaf(a.c.cz[j], tile[lz + j][lx] + tile[lz - j][lx], lap);
+    }
+    const long long gi = static_cast<long long>(gz) * pitch + gx;
+    const float um = a.um[gi];
+    const float bb = a.b[gi];
+    const float sv = a.s[gi];
+    const float dd = c - um;
+    const float bl = bb * lap;
+    a.out[gi] = fmaf(sv, dd, c + dd) + bl;
+    if (MODE == kModeAdjGrad) a.grad[gi] = fmaf(a.neg_inv_dt2 * a.uj[gi], fmaf(sv, dd, bl), a.grad[gi]);
+  }
+}
+
+template <int R, int MODE>
+static cudaError_t launch2d_t(cudaStream_t st, const Stencil2dArgs &a) {
+  dim3 grid((a.g.nx + 31) / 32, (a.g.nz + 15) / 16);
+  stencil2d_kernel<R, MODE><<<grid, dim3(32, 8), 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch2d_m(int R, cudaStream_t st, const Stencil2dArgs &a) {
+  switch (R) {
+    case 1: return launch2d_t<1, MODE>(st, a);
+    case 2: return launch2d_t<2, MODE>(st, a);
+    case 3: return launch2d_t<3, MODE>(st, a);
+    case 4: return launch2d_t<4, MODE>(st, a);
+    case 5: return launch2d_t<5, MODE>(st, a);
+    case 6: return launch2d_t<6, MODE>(st, a);
+    case 7: return launch2d_t<7, MODE>(st, a);
+    case 8: return launch2d_t<8, MODE>(st, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_stencil2d(int R, int mode, cudaStream_t st, const Stencil2dArgs &a) {
+  return mode == kModeAdjGrad ? launch2d_m<kModeAdjGrad>(R, st, a) : launch2d_m<kModeFwd>(R, st, a);
+}
+
+// ---------------------------------------------------------------------------
+// A1: b = dt^2 / (m + eta dt/2) and s = -eta dt / (m + eta dt/2), evaluated in
+// double and stored as float in the pitched layout; per-(plane, tile) damping
+// flags; max(1/m) for the CFL check; non-finite / sign checks of the inputs.
+// ---------------------------------------------------------------------------
+__global__ void coef_kernel(const CoefArgs a) {
+  const long long nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+  const long long n = nx * ny * nz;
+  float local_max = 0.f;
+  int bad = 0;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const float mf = a.m[i], ef = a.eta[i];
+    if (!isfinite(mf) || !isfinite(ef)) bad |= 1;
+    if (!(mf > 0.f) || !(ef >= 0.f)) bad |= 2;
+    const long long x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
+    const double m = mf, e = ef;
+    const double D = m + e * a.dt * 0.5;
+    const long long gi = z * a.g.plane + y * a.g.pitch + x;
+    a.b[gi] = static_cast<float>(a.dt * a.dt / D);
+    a.s[gi] = static_cast<float>(-e * a.dt / D);
+    if (a.tflag && ef != 0.f)
+      a.tflag[(z * a.tiles_y + y / a.tile_h) * a.tiles_x + x / a.tile_w] = 1;
+    if (mf > 0.f) local_max = fmaxf(local_max, 1.0f / mf);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    local_max = fmaxf(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (isfinite(local_max)) atomicMax(a.max_inv_m_bits, __float_as_uint(local_max));
+    else atomicOr(a.bad, 1);
+    if (bad) atomicOr(a.bad, bad);
+  }
+}
+
+cudaError_t launch_coef(cudaStream_t st, const CoefArgs &a) {
+  const long long n = static_cast<long long>(a.g.nx) * a.g.ny * a.g.nz;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  coef_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+__global__ void check_finite_kernel(const float *x, long long n, int *bad) {
+  int b = 0;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    if (!isfinite(x[i])) b = 1;
+  if (b) atomicOr(bad, 1);
+}
+
+cudaError_t launch_check_finite(cudaStream_t st, const float *x, long long n, int *bad) {
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  check_finite_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(x, n, bad);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K2: injection u[t] += b[t] * sum_k w_k q[row][pid_k], one thread per distinct
+// target point, entries summed in a fixed order (deterministic, no atomics).
+// With grad set, also applies the injected part of the gradient bracket:
+// grad[t] -= dt^-2 u^j[t] * b[t] * sum_k w_k q_k.
+// ---------------------------------------------------------------------------
+__global__ void inject_kernel(const InjectArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.ntarget) return;
+  const float *q = a.data + a.row * a.npts;
+  float acc = 0.f;
+  for (int k = a.rowptr[i]; k < a.rowptr[i + 1]; ++k) acc = fmaf(a.w[k], q[a.pid[k]], acc);
+  const long long t = a.target[i];
+  const float inc = a.b[t] * acc;
+  a.u[t] += inc;
+  if (a.grad) a.grad[t] = fmaf(a.neg_inv_dt2 * a.uj[t], inc, a.grad[t]);
+}
+
+cudaError_t launch_inject(cudaStream_t st, const InjectArgs &a) {
+  if (a.ntarget <= 0) return cudaSuccess;
+  inject_kernel<<<(a.ntarget + 127) / 128, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// K3: out[row][i] = sum_c w[i][c] u[idx[i][c]].
+__global__ void interp_kernel(const InterpArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.npts) return;
+  float acc = 0.f;
+  for (int c = 0; c < a.ncorner; ++c) {
+    const long long k = static_cast<long long>(i) * a.ncorner + c;
+    acc = fmaf(a.w[k], a.u[a.idx[k]], acc);
+  }
+  a.out[a.row * a.npts + i] = acc;
+}
+
+cudaError_t launch_interp(cudaStream_t st, const InterpArgs &a) {
+  if (a.npts <= 0) return cudaSuccess;
+  interp_kernel<<<(a.npts + 127) / 128, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace wp

@@ -1,0 +1,87 @@
+// Declarations of the kernel launchers (one translation unit per kernel family).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "wp_device.cuh"
+
+namespace wp {
+
+struct Stencil3dArgs;
+
+// ---- K1, 3D (stencil3d_fwd.cu / stencil3d_adj.cu) ----
+// maps: u (halo box), u^{n-1}, b, s, u^j, g (the last two only in adjoint mode)
+cudaError_t launch_stencil3d_fwd(int R, dim3 grid, cudaStream_t st, const CUtensorMap *maps,
+                                 const Stencil3dArgs &a);
+cudaError_t launch_stencil3d_adj(int R, dim3 grid, cudaStream_t st, const CUtensorMap *maps,
+                                 const Stencil3dArgs &a);
+// sets the dynamic shared-memory limit and reports the CTA footprint / occupancy
+cudaError_t prepare_stencil3d_fwd(int R, int *smem_bytes, int *blocks_per_sm);
+cudaError_t prepare_stencil3d_adj(int R, int *smem_bytes, int *blocks_per_sm);
+
+// ---- K1, 2D (kernels.cu) ----
+struct Stencil2dArgs {
+  FieldGeom g;        // 2D fields use nz rows of `pitch` elements (ny = 1)
+  LapCoef c;
+  const float *u;     // u^n
+  const float *um;    // u^{n-1}
+  const float *b;
+  const float *s;
+  float *out;         // u^{n+1} (may alias um)
+  float *grad;        // adjoint+gradient mode
+  const float *uj;    // adjoint+gradient mode: forward field u^j
+  float neg_inv_dt2;
+};
+cudaError_t launch_stencil2d(int R, int mode, cudaStream_t st, const Stencil2dArgs &a);
+
+// ---- A1: coefficients b, s, damping flags, input checks (kernels.cu) ----
+struct CoefArgs {
+  const float *m;          // contiguous (nz, ny, nx) / (nz, nx)
+  const float *eta;
+  FieldGeom g;
+  double dt;
+  float *b;                // pitched
+  float *s;                // pitched
+  unsigned char *tflag;    // 3D only: [nz][tiles_y][tiles_x], pre-zeroed
+  int tiles_x, tiles_y, tile_w, tile_h;
+  unsigned int *max_inv_m_bits;  // float bits of max(1/m), pre-zeroed
+  int *bad;                // bit 0: non-finite input, bit 1: m <= 0 or eta < 0
+};
+cudaError_t launch_coef(cudaStream_t st, const CoefArgs &a);
+
+// ---- K2: injection, deterministic CSR gather (kernels.cu) ----
+struct InjectArgs {
+  int ntarget;
+  const long long *target;   // pitched flat index of each distinct target point
+  const int *rowptr;         // [ntarget + 1]
+  const int *pid;            // point id of each entry
+  const float *w;            // weight of each entry
+  const float *data;         // [nt][npts]
+  int npts;
+  long long row;             // time row of `data`
+  float *u;                  // field receiving dt^2/(m + eta dt/2) * sum w q
+  const float *b;
+  float *grad;               // optional: gradient correction at the targets
+  const float *uj;
+  float neg_inv_dt2;
+};
+cudaError_t launch_inject(cudaStream_t st, const InjectArgs &a);
+
+// ---- K3: interpolation, gather (kernels.cu) ----
+struct InterpArgs {
+  int npts;
+  int ncorner;               // 4 (2D) or 8 (3D)
+  const long long *idx;      // [npts][ncorner] pitched flat indices
+  const float *w;            // [npts][ncorner]
+  const float *u;
+  float *out;                // [nt][npts]
+  long long row;
+};
+cudaError_t launch_interp(cudaStream_t st, const InterpArgs &a);
+
+// ---- misc ----
+// bit 0 of *bad set if any of x[0..n) is NaN or Inf
+cudaError_t launch_check_finite(cudaStream_t st, const float *x, long long n, int *bad);
+
+}  // namespace wp

@@ -1,0 +1,359 @@
+"""Thin ctypes binding of the C ABI in ``include/wavprop.h`` (same names).
+
+Argument marshalling only: every step of the propagator runs in the CUDA
+library ``libwavprop.so``.  There is no CPU or PyTorch fallback: if the library
+is missing or fails to load, every call raises.
+
+Host-array calls take numpy arrays; device-array calls (``*_dev``) take CUDA
+torch tensors (contiguous float32) and run ordered on the current torch stream.
+Coordinates are (npoints, ndim) float64 arrays in the axis order of ``shape``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwavprop.so")
+
+WP_OK, WP_EINVAL, WP_ECFL, WP_ENOMEM, WP_ENONFINITE, WP_ECUDA, WP_ETIMEOUT, WP_EDEVICE = 0, -1, -2, -3, -4, -5, -6, -7
+WP_BUDGET_AUTO = ctypes.c_size_t(-1).value
+STATUS_NAMES = {0: "WP_OK", -1: "WP_EINVAL", -2: "WP_ECFL", -3: "WP_ENOMEM", -4: "WP_ENONFINITE",
+                -5: "WP_ECUDA", -6: "WP_ETIMEOUT", -7: "WP_EDEVICE"}
+
+EXPORTED = [
+    "wp_create", "wp_destroy", "wp_last_error", "wp_set_timeout", "wp_fd_weights", "wp_cfl_dt",
+    "wp_estimate_bytes", "wp_forward", "wp_adjoint", "wp_gradient", "wp_forward_dev", "wp_adjoint_dev",
+    "wp_gradient_dev", "wp_propagate_dev", "wp_forward_save", "wp_backward", "wp_state_free",
+    "wp_bytes_in_use", "wp_kernel_launches", "wp_set_profiling", "wp_profile_read",
+]
+
+
+class WpError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class wp_grid(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int),
+        ("shape", ctypes.c_int64 * 3),
+        ("spacing", ctypes.c_double * 3),
+        ("origin", ctypes.c_double * 3),
+        ("space_order", ctypes.c_int),
+        ("dt", ctypes.c_double),
+        ("nt", ctypes.c_int),
+    ]
+
+
+@dataclass
+class Grid:
+    """Geometry of one problem (mirrors ``wp_grid``)."""
+
+    shape: tuple
+    spacing: tuple
+    origin: tuple
+    space_order: int
+    dt: float = 0.0
+    nt: int = 0
+
+    @property
+    def ndim(self) -> int:
+        return len(self.shape)
+
+    def c(self) -> wp_grid:
+        g = wp_grid()
+        g.ndim = len(self.shape)
+        for i, (n, h, o) in enumerate(zip(self.shape, self.spacing, self.origin)):
+            g.shape[i] = int(n)
+            g.spacing[i] = float(h)
+            g.origin[i] = float(o)
+        g.space_order = int(self.space_order)
+        g.dt = float(self.dt)
+        g.nt = int(self.nt)
+        return g
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_gp = ctypes.POINTER(wp_grid)
+_i = ctypes.c_int
+_fp = ctypes.c_void_p  # float* (host or device address)
+_dp = ctypes.c_void_p  # double* (host)
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``libwavprop.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it first (python -m paper_1808_01995_gb300.build); "
+                           "there is no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "wp_create": ([ctypes.POINTER(_vp), _i, ctypes.c_size_t], _i),
+        "wp_destroy": ([_vp], None),
+        "wp_last_error": ([], ctypes.c_char_p),
+        "wp_set_timeout": ([_vp, ctypes.c_double], _i),
+        "wp_fd_weights": ([_i, _dp], _i),
+        "wp_cfl_dt": ([_gp, ctypes.c_double, ctypes.POINTER(ctypes.c_double)], _i),
+        "wp_estimate_bytes": ([_gp, _i, _i, _i, _i, ctypes.POINTER(ctypes.c_size_t)], _i),
+        "wp_forward": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _i, _dp, _fp], _i),
+        "wp_adjoint": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _i, _dp, _fp], _i),
+        "wp_gradient": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _fp, _i, _dp, _i, _fp], _i),
+        "wp_forward_dev": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _i, _dp, _fp, _vp], _i),
+        "wp_adjoint_dev": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _i, _dp, _fp, _vp], _i),
+        "wp_gradient_dev": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _fp, _i, _dp, _i, _fp, _vp], _i),
+        "wp_propagate_dev": ([_vp, _gp, _fp, _fp, _fp, _fp, _i, _vp], _i),
+        "wp_forward_save": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _i, _dp, _i, _fp, _vp, ctypes.POINTER(_vp)], _i),
+        "wp_backward": ([_vp, _fp, _fp, _vp], _i),
+        "wp_state_free": ([_vp], None),
+        "wp_bytes_in_use": ([_vp], ctypes.c_size_t),
+        "wp_kernel_launches": ([_vp], ctypes.c_uint64),
+        "wp_set_profiling": ([_vp, _i], _i),
+        "wp_profile_read": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64), _i], _i),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != WP_OK:
+        msg = lib().wp_last_error()
+        raise WpError(rc, msg.decode() if msg else "")
+
+
+def _host_f32(a, shape=None):
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    if shape is not None:
+        arr = arr.reshape(shape)
+    return arr
+
+
+def _coords(c, ndim):
+    if c is None:
+        return np.zeros((0, ndim))
+    return np.ascontiguousarray(np.asarray(c, dtype=np.float64)).reshape(-1, ndim)
+
+
+def _ptr(a):
+    """Address of a numpy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data if a.size else None
+    return a.data_ptr() if a.numel() else None
+
+
+def _dev_f32(t, what):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{what} must be a contiguous float32 CUDA tensor")
+    return t
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+# ---------------------------------------------------------------------------
+# context
+# ---------------------------------------------------------------------------
+
+def wp_create(device: int = 0, hbm_budget_bytes: int = WP_BUDGET_AUTO) -> int:
+    h = _vp()
+    _check(lib().wp_create(ctypes.byref(h), int(device), ctypes.c_size_t(hbm_budget_bytes)))
+    return h.value
+
+
+def wp_destroy(ctx: int) -> None:
+    lib().wp_destroy(ctx)
+
+
+def wp_last_error() -> str:
+    m = lib().wp_last_error()
+    return m.decode() if m else ""
+
+
+def wp_set_timeout(ctx: int, seconds: float) -> None:
+    _check(lib().wp_set_timeout(ctx, float(seconds)))
+
+
+def wp_bytes_in_use(ctx: int) -> int:
+    return int(lib().wp_bytes_in_use(ctx))
+
+
+def wp_kernel_launches(ctx: int) -> int:
+    return int(lib().wp_kernel_launches(ctx))
+
+
+def wp_set_profiling(ctx: int, enabled: bool) -> None:
+    _check(lib().wp_set_profiling(ctx, 1 if enabled else 0))
+
+
+def wp_profile_read(ctx: int, reset: bool = True):
+    """(summed stencil device time in ms, number of stencil launches)."""
+    ms = ctypes.c_double()
+    n = ctypes.c_uint64()
+    _check(lib().wp_profile_read(ctx, ctypes.byref(ms), ctypes.byref(n), 1 if reset else 0))
+    return ms.value, int(n.value)
+
+
+def wp_fd_weights(space_order: int) -> np.ndarray:
+    a = np.zeros(9)
+    _check(lib().wp_fd_weights(int(space_order), a.ctypes.data))
+    return a[: space_order // 2 + 1].copy()
+
+
+def wp_cfl_dt(grid: Grid, vmax: float) -> float:
+    out = ctypes.c_double()
+    g = grid.c()
+    _check(lib().wp_cfl_dt(ctypes.byref(g), float(vmax), ctypes.byref(out)))
+    return out.value
+
+
+def wp_estimate_bytes(grid: Grid, nsrc: int, nrec: int, mode: int = 0, snap_interval: int = 1) -> int:
+    out = ctypes.c_size_t()
+    g = grid.c()
+    _check(lib().wp_estimate_bytes(ctypes.byref(g), int(nsrc), int(nrec), int(mode), int(snap_interval),
+                                   ctypes.byref(out)))
+    return int(out.value)
+
+
+# ---------------------------------------------------------------------------
+# host-array calls
+# ---------------------------------------------------------------------------
+
+def wp_forward(ctx: int, grid: Grid, m, eta, wavelet, src, rec) -> np.ndarray:
+    m = _host_f32(m, grid.shape)
+    eta = _host_f32(eta, grid.shape)
+    src = _coords(src, grid.ndim)
+    rec = _coords(rec, grid.ndim)
+    q = _host_f32(wavelet if wavelet is not None else np.zeros((grid.nt, 0)), (grid.nt, len(src)))
+    out = np.zeros((grid.nt, len(rec)), dtype=np.float32)
+    g = grid.c()
+    _check(lib().wp_forward(ctx, ctypes.byref(g), _ptr(m), _ptr(eta), _ptr(q), len(src), _ptr(src), len(rec),
+                            _ptr(rec), _ptr(out)))
+    return out
+
+
+def wp_adjoint(ctx: int, grid: Grid, m, eta, rec_data, rec, src) -> np.ndarray:
+    m = _host_f32(m, grid.shape)
+    eta = _host_f32(eta, grid.shape)
+    src = _coords(src, grid.ndim)
+    rec = _coords(rec, grid.ndim)
+    d = _host_f32(rec_data, (grid.nt, len(rec)))
+    out = np.zeros((grid.nt, len(src)), dtype=np.float32)
+    g = grid.c()
+    _check(lib().wp_adjoint(ctx, ctypes.byref(g), _ptr(m), _ptr(eta), _ptr(d), len(rec), _ptr(rec), len(src),
+                            _ptr(src), _ptr(out)))
+    return out
+
+
+def wp_gradient(ctx: int, grid: Grid, m, eta, wavelet, src, residual, rec, snap_interval: int) -> np.ndarray:
+    m = _host_f32(m, grid.shape)
+    eta = _host_f32(eta, grid.shape)
+    src = _coords(src, grid.ndim)
+    rec = _coords(rec, grid.ndim)
+    q = _host_f32(wavelet, (grid.nt, len(src)))
+    r = _host_f32(residual, (grid.nt, len(rec)))
+    out = np.zeros(grid.shape, dtype=np.float32)
+    g = grid.c()
+    _check(lib().wp_gradient(ctx, ctypes.byref(g), _ptr(m), _ptr(eta), _ptr(q), len(src), _ptr(src), _ptr(r),
+                             len(rec), _ptr(rec), int(snap_interval), _ptr(out)))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# device-array calls (torch tensors)
+# ---------------------------------------------------------------------------
+
+def wp_forward_dev(ctx: int, grid: Grid, m, eta, wavelet, src, rec, rec_out, stream=None) -> None:
+    src = _coords(src, grid.ndim)
+    rec = _coords(rec, grid.ndim)
+    g = grid.c()
+    _check(lib().wp_forward_dev(ctx, ctypes.byref(g), _ptr(_dev_f32(m, "m")), _ptr(_dev_f32(eta, "eta")),
+                                _ptr(wavelet), len(src), _ptr(src), len(rec), _ptr(rec), _ptr(rec_out),
+                                _stream(stream)))
+
+
+def wp_adjoint_dev(ctx: int, grid: Grid, m, eta, rec_data, rec, src, src_out, stream=None) -> None:
+    src = _coords(src, grid.ndim)
+    rec = _coords(rec, grid.ndim)
+    g = grid.c()
+    _check(lib().wp_adjoint_dev(ctx, ctypes.byref(g), _ptr(_dev_f32(m, "m")), _ptr(_dev_f32(eta, "eta")),
+                                _ptr(rec_data), len(rec), _ptr(rec), len(src), _ptr(src), _ptr(src_out),
+                                _stream(stream)))
+
+
+def wp_gradient_dev(ctx: int, grid: Grid, m, eta, wavelet, src, residual, rec, snap_interval, grad_out,
+                    stream=None) -> None:
+    src = _coords(src, grid.ndim)
+    rec = _coords(rec, grid.ndim)
+    g = grid.c()
+    _check(lib().wp_gradient_dev(ctx, ctypes.byref(g), _ptr(_dev_f32(m, "m")), _ptr(_dev_f32(eta, "eta")),
+                                 _ptr(wavelet), len(src), _ptr(src), _ptr(residual), len(rec), _ptr(rec),
+                                 int(snap_interval), _ptr(_dev_f32(grad_out, "grad_out")), _stream(stream)))
+
+
+def wp_propagate_dev(ctx: int, grid: Grid, m, eta, u_prev, u, nsteps: int, stream=None) -> None:
+    g = grid.c()
+    _check(lib().wp_propagate_dev(ctx, ctypes.byref(g), _ptr(_dev_f32(m, "m")), _ptr(_dev_f32(eta, "eta")),
+                                  _ptr(_dev_f32(u_prev, "u_prev")), _ptr(_dev_f32(u, "u")), int(nsteps),
+                                  _stream(stream)))
+
+
+def wp_forward_save(ctx: int, grid: Grid, m, eta, wavelet, src, rec, snap_interval: int, rec_out,
+                    stream=None) -> int:
+    src = _coords(src, grid.ndim)
+    rec = _coords(rec, grid.ndim)
+    g = grid.c()
+    st = _vp()
+    _check(lib().wp_forward_save(ctx, ctypes.byref(g), _ptr(_dev_f32(m, "m")), _ptr(_dev_f32(eta, "eta")),
+                                 _ptr(wavelet), len(src), _ptr(src), len(rec), _ptr(rec), int(snap_interval),
+                                 _ptr(rec_out), _stream(stream), ctypes.byref(st)))
+    return st.value
+
+
+def wp_backward(state: int, residual, grad_out, stream=None) -> None:
+    _check(lib().wp_backward(state, _ptr(residual), _ptr(_dev_f32(grad_out, "grad_out")), _stream(stream)))
+
+
+def wp_state_free(state: int) -> None:
+    lib().wp_state_free(state)
+
+
+class Context:
+    """Owns a ``wp_ctx`` (device memory pool, stream); closes on ``close()``/exit."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = WP_BUDGET_AUTO):
+        self.handle = wp_create(device, hbm_budget_bytes)
+
+    def close(self):
+        if self.handle:
+            wp_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
