@@ -419,6 +419,7 @@ static int get_encode() {
 
 // 3D map over a pitched field, box (bx, by, 1); out-of-range elements read as 0.
 static int make_map(CUtensorMap *m, const float *base, const Geom &G, int bx, int by) {
+  TRY(get_encode());
   cuuint64_t dims[3] = {cuuint64_t(G.nx), cuuint64_t(G.ny), cuuint64_t(G.nz)};
   cuuint64_t strides[2] = {cuuint64_t(G.pitch) * 4, cuuint64_t(G.plane) * 4};
   cuuint32_t box[3] = {cuuint32_t(bx), cuuint32_t(by), 1};
@@ -500,7 +501,6 @@ static int prop_setup(wp_ctx *c, Arena &ar, const Geom &G, const float *m, const
   if (G.dt > lim * (1.0 + 1e-5))
     return fail(WP_ECFL, "dt = %.6g exceeds the stability limit %.6g for vmax = %.6g", G.dt, lim, vmax);
   if (G.ndim == 3) {
-    TRY(get_encode());
     TRY(make_field_maps(&P->b, G));
     TRY(make_field_maps(&P->s, G));
     const int ntile = G.tiles_x * G.tiles_y;
@@ -929,6 +929,7 @@ int wp_create(wp_ctx **out, int device, size_t budget) {
     CU(cudaMalloc(&c->d_scalars, 64));
     CU(cudaMallocHost(&c->h_scalars, 64));
     CU(cudaMemset(c->d_scalars, 0, 64));
+    TRY(get_encode());
     for (int R = 1; R <= 8; ++R) {
       CU(prepare_stencil3d_fwd(R, &c->smem3d[0][R], &c->occ3d[0][R]));
       CU(prepare_stencil3d_adj(R, &c->smem3d[1][R], &c->occ3d[1][R]));
