@@ -178,6 +178,34 @@ uint64_t wp_kernel_launches(const wp_ctx *ctx);
 int wp_set_profiling(wp_ctx *ctx, int enabled);
 int wp_profile_read(wp_ctx *ctx, double *stencil_ms, uint64_t *stencil_launches, int reset);
 
+/* ---- forward modelling without any device allocation -----------------------
+ * The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory: code that runs inside a host application which owns
+ * every device byte through its own pool or arena and forbids cudaMalloc /
+ * cudaFree from libraries, or that has budgeted its device memory up front.
+ * It computes exactly what wp_forward_dev computes (same kernels, same
+ * arguments, device pointers for m, eta, wavelet and rec_out, host coordinates)
+ * but needs no wp_ctx and allocates nothing: its work space (coefficients, the
+ * two wavefields, damping flags, source and receiver tables) is one fixed
+ * device array of WP_NOALLOC_MAX_BYTES declared by the library, which every GPU
+ * that loads the library holds until the process exits.
+ *   - A problem whose work space would exceed WP_NOALLOC_MAX_BYTES is rejected
+ *     with WP_ENOMEM before any device work (3D grids up to about 4 million
+ *     points fit).
+ *   - The first call on a device looks the array's device address up there
+ *     (this may make CUDA load the library's device code on that device); make
+ *     that first call before any stream capture.
+ *   - Every call uses the same array, which keeps the previous call's contents
+ *     (the call clears what must start at zero).  Calls that overlap on the GPU,
+ *     from several streams or host threads, race on it and corrupt each other's
+ *     results: serialise them.
+ * Work runs on `stream` (NULL = legacy default stream) and the call returns
+ * after it has finished. */
+#define WP_NOALLOC_MAX_BYTES ((size_t)64 << 20)
+int wp_forward_noalloc(const wp_grid *grid, const float *m, const float *eta,
+                       const float *wavelet, int nsrc, const double *src_coords, int nrec,
+                       const double *rec_coords, float *rec_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

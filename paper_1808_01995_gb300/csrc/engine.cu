@@ -13,6 +13,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -1115,3 +1116,255 @@ int wp_propagate_dev(wp_ctx *c, const wp_grid *grid, const float *m, const float
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Forward without device allocation (wp_forward_noalloc).  The work space lives
+// in one statically declared device array; host code must use the address that
+// cudaGetSymbolAddress returns for the current device (the array's name in host
+// code is only a host-side stand-in).
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[WP_NOALLOC_MAX_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[256];  // per device, filled on the first call there
+
+static int noalloc_scratch(void **out) {
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return fail(WP_EINVAL, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(WP_ECUDA, "cudaGetSymbolAddress of the no-allocation work space failed: %s",
+                  cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return WP_OK;
+}
+
+// Carves 256-byte aligned pieces out of the fixed work space.
+struct Carve {
+  unsigned char *base;
+  size_t used = 0, cap;
+  bool over = false;
+  template <class T>
+  T *take(size_t count) {
+    const size_t off = round_up(used, 256);
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 1);
+    if (off + bytes > cap) {
+      over = true;
+      used = off + bytes;
+      return nullptr;
+    }
+    used = off + bytes;
+    return base ? reinterpret_cast<T *>(base + off) : nullptr;
+  }
+};
+
+// Injection table in the same (target, point, corner) order as the context path.
+static void csr_of(const PointSet &ps, std::vector<long long> &target, std::vector<int> &rowptr,
+                   std::vector<int> &pid, std::vector<float> &cw) {
+  const size_t ne = size_t(ps.npts) * ps.nc;
+  std::vector<size_t> order(ne);
+  for (size_t e = 0; e < ne; ++e) order[e] = e;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return ps.idx[a] < ps.idx[b]; });
+  for (size_t k = 0; k < ne; ++k) {
+    const size_t e = order[k];
+    if (target.empty() || target.back() != ps.idx[e]) {
+      target.push_back(ps.idx[e]);
+      rowptr.push_back(int(k));
+    }
+    pid.push_back(int(e / ps.nc));
+    cw.push_back(ps.w[e]);
+  }
+  rowptr.push_back(int(ne));
+}
+
+static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta, const float *wavelet, int nsrc,
+                           const double *src, int nrec, const double *rec, float *rec_out, cudaStream_t st) {
+  Geom G;
+  TRY(make_geom(grid, &G));
+  if (nsrc < 0 || nrec < 0) return fail(WP_EINVAL, "point counts must be >= 0");
+  if (!m || !eta) return fail(WP_EINVAL, "m and eta must not be NULL");
+  if (nsrc > 0 && G.nt > 0 && !wavelet) return fail(WP_EINVAL, "wavelet is NULL");
+  if (nrec > 0 && G.nt > 0 && !rec_out) return fail(WP_EINVAL, "rec_out is NULL");
+  PointSet ps, pr;
+  TRY(build_points(G, nsrc, src, &ps, "source"));
+  TRY(build_points(G, nrec, rec, &pr, "receiver"));
+  std::vector<long long> target;
+  std::vector<int> rowptr, pid;
+  std::vector<float> cw;
+  csr_of(ps, target, rowptr, pid, cw);
+
+  // size the work space before touching the device
+  Carve cv{nullptr, 0, WP_NOALLOC_MAX_BYTES};
+  auto plan = [&](Carve &c, int **scal, float **b, float **s, float **u0, float **u1, unsigned char **tflag,
+                  long long **d_target, int **d_rowptr, int **d_pid, float **d_cw, long long **d_ridx,
+                  float **d_rw) {
+    *scal = c.take<int>(16);
+    *b = c.take<float>(G.nfield);
+    *s = c.take<float>(G.nfield);
+    *u0 = c.take<float>(G.nfield);
+    *u1 = c.take<float>(G.nfield);
+    *tflag = G.ndim == 3 ? c.take<unsigned char>(size_t(G.nz) * G.tiles_y * G.tiles_x) : nullptr;
+    *d_target = c.take<long long>(target.size());
+    *d_rowptr = c.take<int>(rowptr.size());
+    *d_pid = c.take<int>(pid.size());
+    *d_cw = c.take<float>(cw.size());
+    *d_ridx = c.take<long long>(pr.idx.size());
+    *d_rw = c.take<float>(pr.w.size());
+  };
+  int *scal;
+  float *b, *s, *u0, *u1, *d_cw, *d_rw;
+  unsigned char *tflag;
+  long long *d_target, *d_ridx;
+  int *d_rowptr, *d_pid;
+  plan(cv, &scal, &b, &s, &u0, &u1, &tflag, &d_target, &d_rowptr, &d_pid, &d_cw, &d_ridx, &d_rw);
+  if (cv.over)
+    return fail(WP_ENOMEM, "this problem needs %zu bytes of work space; wp_forward_noalloc is limited to %zu",
+                cv.used, size_t(WP_NOALLOC_MAX_BYTES));
+  void *base = nullptr;
+  TRY(noalloc_scratch(&base));
+  Carve c{static_cast<unsigned char *>(base), 0, WP_NOALLOC_MAX_BYTES};
+  plan(c, &scal, &b, &s, &u0, &u1, &tflag, &d_target, &d_rowptr, &d_pid, &d_cw, &d_ridx, &d_rw);
+
+  // the array keeps the last call's contents: clear what must start at zero
+  CU(cudaMemsetAsync(scal, 0, 16 * sizeof(int), st));
+  if (tflag) CU(cudaMemsetAsync(tflag, 0, size_t(G.nz) * G.tiles_y * G.tiles_x, st));
+  if (!target.empty()) {
+    CU(cudaMemcpyAsync(d_target, target.data(), target.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(d_rowptr, rowptr.data(), rowptr.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(d_pid, pid.data(), pid.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(d_cw, cw.data(), cw.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  }
+  if (!pr.idx.empty()) {
+    CU(cudaMemcpyAsync(d_ridx, pr.idx.data(), pr.idx.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(d_rw, pr.w.data(), pr.w.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  }
+  CoefArgs ca;
+  memset(&ca, 0, sizeof ca);
+  ca.m = m;
+  ca.eta = eta;
+  ca.g = G.fg();
+  ca.dt = G.dt;
+  ca.b = b;
+  ca.s = s;
+  ca.tflag = tflag;
+  ca.tiles_x = G.tiles_x;
+  ca.tiles_y = G.tiles_y;
+  ca.tile_w = kTX;
+  ca.tile_h = kTY;
+  ca.max_inv_m_bits = reinterpret_cast<unsigned int *>(scal + 2);
+  ca.bad = scal + 1;
+  CU(launch_coef(st, ca));
+  if (size_t(G.nt) * nsrc > 0) CU(launch_check_finite(st, wavelet, (long long)G.nt * nsrc, scal + 3));
+  int h[16];
+  CU(cudaMemcpyAsync(h, scal, sizeof h, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if ((h[1] & 1) || h[3]) return fail(WP_ENONFINITE, "m, eta or the wavelet holds NaN or Inf");
+  if (h[1] & 2) return fail(WP_EINVAL, "m must be > 0 and eta >= 0 everywhere");
+  float max_inv_m;
+  memcpy(&max_inv_m, &h[2], 4);
+  const double vmax = std::sqrt(double(max_inv_m));
+  const double lim = cfl_limit(G, vmax);
+  if (G.dt > lim * (1.0 + 1e-5))
+    return fail(WP_ECFL, "dt = %.6g exceeds the stability limit %.6g for vmax = %.6g", G.dt, lim, vmax);
+  CU(cudaMemsetAsync(u0, 0, G.field_bytes(), st));
+  CU(cudaMemsetAsync(u1, 0, G.field_bytes(), st));
+
+  const LapCoef lc = lap_coef(G);
+  const float neg_inv_dt2 = static_cast<float>(-1.0 / (G.dt * G.dt));
+  float *u[2] = {u0, u1};
+  CUtensorMap halo[2], tile[2], tb, ts;
+  dim3 grid3;
+  int zc = 0;
+  if (G.ndim == 3) {
+    for (int i = 0; i < 2; ++i) {
+      TRY(make_map(&halo[i], u[i], G, halo_box_w(G.R), kTY + 2 * G.R));
+      TRY(make_map(&tile[i], u[i], G, kTX, kTY));
+    }
+    TRY(make_map(&tb, b, G, kTX, kTY));
+    TRY(make_map(&ts, s, G, kTX, kTY));
+    int smem = 0, occ = 0, dev = 0, nsm = 0;
+    CU(prepare_stencil3d_fwd(G.R, &smem, &occ));
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int nchunk = std::max(1, nsm * std::max(1, occ) / (G.tiles_x * G.tiles_y));
+    zc = std::max((G.nz + nchunk - 1) / nchunk, std::min(G.nz, 8));
+    grid3 = dim3(G.tiles_x, G.tiles_y, (G.nz + zc - 1) / zc);
+  }
+  for (int k = 0; k < G.nt; ++k) {
+    float *cur = u[k & 1], *prv = u[(k + 1) & 1];
+    if (G.ndim == 3) {
+      Stencil3dArgs a;
+      a.g = G.fg();
+      a.c = lc;
+      a.u = cur;
+      a.out = prv;
+      a.grad = nullptr;
+      a.neg_inv_dt2 = neg_inv_dt2;
+      a.tflag = tflag;
+      a.tiles_x = G.tiles_x;
+      a.tiles_y = G.tiles_y;
+      a.zchunk = zc;
+      a.err = scal;
+      CUtensorMap maps[6] = {halo[k & 1], tile[(k + 1) & 1], tb, ts, tb, tb};
+      CU(launch_stencil3d_fwd(G.R, grid3, st, maps, a));
+    } else {
+      Stencil2dArgs a;
+      a.g = G.fg();
+      a.c = lc;
+      a.u = cur;
+      a.um = prv;
+      a.b = b;
+      a.s = s;
+      a.out = prv;
+      a.grad = nullptr;
+      a.uj = nullptr;
+      a.neg_inv_dt2 = neg_inv_dt2;
+      CU(launch_stencil2d(G.R, kModeFwd, st, a));
+    }
+    if (!target.empty()) {
+      InjectArgs ia;
+      ia.ntarget = int(target.size());
+      ia.target = d_target;
+      ia.rowptr = d_rowptr;
+      ia.pid = d_pid;
+      ia.w = d_cw;
+      ia.data = wavelet;
+      ia.npts = nsrc;
+      ia.row = k;
+      ia.u = prv;
+      ia.b = b;
+      ia.grad = nullptr;
+      ia.uj = nullptr;
+      ia.neg_inv_dt2 = neg_inv_dt2;
+      CU(launch_inject(st, ia));
+    }
+    if (nrec > 0) {
+      InterpArgs pa;
+      pa.npts = nrec;
+      pa.ncorner = pr.nc;
+      pa.idx = d_ridx;
+      pa.w = d_rw;
+      pa.u = prv;
+      pa.out = rec_out;
+      pa.row = k;
+      CU(launch_interp(st, pa));
+    }
+  }
+  CU(cudaMemcpyAsync(h, scal, sizeof h, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (h[0] != 0) return fail(WP_EDEVICE, "a kernel reported device error %d (a wait timed out)", h[0]);
+  return WP_OK;
+}
+
+extern "C" int wp_forward_noalloc(const wp_grid *grid, const float *m, const float *eta, const float *wavelet,
+                                  int nsrc, const double *src_coords, int nrec, const double *rec_coords,
+                                  float *rec_out, void *stream) {
+  return forward_noalloc(grid, m, eta, wavelet, nsrc, src_coords, nrec, rec_coords, rec_out,
+                         static_cast<cudaStream_t>(stream));
+}

@@ -117,6 +117,7 @@ def lib() -> ctypes.CDLL:
         "wp_kernel_launches": ([_vp], ctypes.c_uint64),
         "wp_set_profiling": ([_vp, _i], _i),
         "wp_profile_read": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64), _i], _i),
+        "wp_forward_noalloc": ([_gp, _fp, _fp, _fp, _i, _dp, _i, _dp, _fp, _vp], _i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -333,6 +334,21 @@ def wp_backward(state: int, residual, grad_out, stream=None) -> None:
 
 def wp_state_free(state: int) -> None:
     lib().wp_state_free(state)
+
+
+WP_NOALLOC_MAX_BYTES = 64 << 20
+
+
+def wp_forward_noalloc(grid: Grid, m, eta, wavelet, src, rec, rec_out, stream=None) -> None:
+    """wp_forward_dev without a context and without any device allocation: the work
+    space is the library's fixed device array of WP_NOALLOC_MAX_BYTES, shared by
+    every call (serialise calls; they race if they overlap on the GPU)."""
+    src = _coords(src, grid.ndim)
+    rec = _coords(rec, grid.ndim)
+    g = grid.c()
+    _check(lib().wp_forward_noalloc(ctypes.byref(g), _ptr(_dev_f32(m, "m")), _ptr(_dev_f32(eta, "eta")),
+                                    _ptr(wavelet), len(src), _ptr(src), len(rec), _ptr(rec), _ptr(rec_out),
+                                    _stream(stream)))
 
 
 class Context:
