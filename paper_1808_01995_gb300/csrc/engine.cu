@@ -69,6 +69,7 @@ struct wp_ctx {
   uint64_t launches = 0;
   int smem3d[2][9] = {};
   int occ3d[2][9] = {};
+  int ty3d[2][9] = {};
   bool broken = false;
   // profiling: an event pair around every stencil launch, summed on read
   bool profiling = false;
@@ -149,19 +150,20 @@ struct Arena {
   }
 };
 
-// Wait for everything queued on the context stream, with a deadline.
-static int ctx_wait(wp_ctx *c) {
+// Wait for everything queued on the context stream, with a deadline; `what`
+// names the phase in error messages.
+static int ctx_wait(wp_ctx *c, const char *what = "device work") {
   CU(cudaEventRecord(c->ev_done, c->stream));
   const auto t0 = std::chrono::steady_clock::now();
   int spins = 0;
   while (true) {
     cudaError_t e = cudaEventQuery(c->ev_done);
     if (e == cudaSuccess) break;
-    if (e != cudaErrorNotReady) return fail(WP_ECUDA, "device work failed: %s", cudaGetErrorString(e));
+    if (e != cudaErrorNotReady) return fail(WP_ECUDA, "%s failed: %s", what, cudaGetErrorString(e));
     const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (dt > c->timeout_s) {
       c->broken = true;
-      return fail(WP_ETIMEOUT, "device work did not finish within %.1f s", c->timeout_s);
+      return fail(WP_ETIMEOUT, "%s did not finish within %.1f s", what, c->timeout_s);
     }
     if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(spins > 1000 ? 200 : 20));
   }
@@ -191,7 +193,8 @@ struct Geom {
   int k = 0, R = 0;
   double dt = 0;
   int nt = 0;
-  int tiles_x = 1, tiles_y = 1;
+  int tiles_x = 1, tiles_y = 1;  // damping-flag tiles (32 x 16)
+  int nzw = 1;                    // 32-bit words of a tile's z bitmask
   FieldGeom fg() const {
     FieldGeom g;
     g.nx = nx;
@@ -277,7 +280,8 @@ static int make_geom(const wp_grid *g, Geom *G, bool need_dt = true) {
   G->npoints = static_cast<long long>(G->nx) * G->ny * G->nz;
   if (G->nfield > (1ll << 36)) return fail(WP_EINVAL, "grid too large");
   G->tiles_x = (G->nx + kTX - 1) / kTX;
-  G->tiles_y = (G->ny + kTY - 1) / kTY;
+  G->tiles_y = (G->ny + kTileFlagTY - 1) / kTileFlagTY;  // damping-flag rows
+  G->nzw = (G->nz + 31) / 32;
   return WP_OK;
 }
 
@@ -434,17 +438,65 @@ static int make_map(CUtensorMap *m, const float *base, const Geom &G, int bx, in
 
 static int halo_box_w(int R) { return kTX + 2 * ((R + 3) / 4 * 4); }
 
-// A field and its two descriptors (halo'd plane box, tile box).
+// A field and its TMA descriptors: the halo'd plane box of the forward and of the
+// adjoint+gradient stencil (their tiles differ in height).
 struct Field3 {
   float *p = nullptr;
-  CUtensorMap halo, tile;
+  bool mapped = false;  // descriptors encoded for p
+  CUtensorMap halo[2], tile[2];
 };
 
 static int make_field_maps(Field3 *f, const Geom &G) {
   if (G.ndim != 3) return WP_OK;
-  TRY(make_map(&f->halo, f->p, G, halo_box_w(G.R), kTY + 2 * G.R));
-  TRY(make_map(&f->tile, f->p, G, kTX, kTY));
+  for (int mode = 0; mode < 2; ++mode) {
+    const int ty = stencil3d_tile_y(G.R, mode);
+    TRY(make_map(&f->halo[mode], f->p, G, halo_box_w(G.R), ty + 2 * G.R));
+    TRY(make_map(&f->tile[mode], f->p, G, kTX, ty));
+  }
+  f->mapped = true;
   return WP_OK;
+}
+
+// Persistent launch plan of the 3D stencil: (tile, z-chunk) work items walked
+// round-robin by ctas = SMs x occupancy CTAs.  The chunk count minimises
+// rounds x (chunk + R), the planes streamed by the busiest CTA.
+struct Plan3d {
+  int tiles_x = 1, tiles_y = 1, zchunk = 1, nzc = 1, nitems = 0;
+  dim3 grid;
+};
+
+static Plan3d plan3d(const Geom &G, int mode, int num_sms, int occ) {
+  Plan3d p;
+  const int ty = stencil3d_tile_y(G.R, mode);
+  p.tiles_x = (G.nx + kTX - 1) / kTX;
+  p.tiles_y = (G.ny + ty - 1) / ty;
+  const long long tiles = static_cast<long long>(p.tiles_x) * p.tiles_y;
+  const long long ctas = static_cast<long long>(num_sms) * std::max(occ, 1);
+  double best = 1e300;
+  const int min_chunk = std::min(G.nz, std::max(2 * G.R, 8));
+  for (int nzc = 1; nzc <= G.nz; ++nzc) {
+    const int zc = (G.nz + nzc - 1) / nzc;
+    if (zc < min_chunk) break;
+    const int n_eff = (G.nz + zc - 1) / zc;
+    const long long items = tiles * n_eff;
+    const long long rounds = (items + ctas - 1) / ctas;
+    const double used = std::min(1.0, double(items) / double(ctas));
+    // fewer CTAs than slots leave bandwidth unused: charge the idle fraction
+    const double cost = double(rounds) * (zc + G.R) / std::min(1.0, used / 0.9);
+    if (cost < best * 0.999) {
+      best = cost;
+      p.zchunk = zc;
+      p.nzc = n_eff;
+    }
+  }
+  const char *env = getenv("WP_ZCHUNK");
+  if (env && atoi(env) > 0) {
+    p.zchunk = std::min(G.nz, atoi(env));
+    p.nzc = (G.nz + p.zchunk - 1) / p.zchunk;
+  }
+  p.nitems = int(tiles * p.nzc);
+  p.grid = dim3(unsigned(std::min<long long>(p.nitems, ctas)));
+  return p;
 }
 
 // ---------------------------------------------------------------------------
@@ -456,9 +508,8 @@ struct Prop {
   LapCoef lc;
   float neg_inv_dt2 = 0;
   Field3 b, s;
-  unsigned char *tflag = nullptr;
-  dim3 grid3;
-  int zchunk = 0;
+  unsigned *tbits = nullptr;
+  Plan3d plan[2];
 };
 
 static int prop_setup(wp_ctx *c, Arena &ar, const Geom &G, const float *m, const float *eta, Prop *P) {
@@ -479,20 +530,24 @@ static int prop_setup(wp_ctx *c, Arena &ar, const Geom &G, const float *m, const
   a.s = P->s.p;
   if (G.ndim == 3) {
     const size_t nflag = size_t(G.nz) * G.tiles_y * G.tiles_x;
-    TRY(ar.alloc(&P->tflag, nflag));
-    CU(cudaMemsetAsync(P->tflag, 0, nflag, c->stream));
-    a.tflag = P->tflag;
+    unsigned char *tflag = nullptr;
+    TRY(ar.alloc(&tflag, nflag));
+    CU(cudaMemsetAsync(tflag, 0, nflag, c->stream));
+    TRY(ar.alloc(&P->tbits, size_t(G.tiles_y) * G.tiles_x * G.nzw));
+    a.tflag = tflag;
+    a.tbits = P->tbits;
+    a.nzw = G.nzw;
     a.tiles_x = G.tiles_x;
     a.tiles_y = G.tiles_y;
     a.tile_w = kTX;
-    a.tile_h = kTY;
+    a.tile_h = kTileFlagTY;
   }
   a.max_inv_m_bits = reinterpret_cast<unsigned int *>(c->d_scalars + 2);
   a.bad = c->d_scalars + 1;
   CU(launch_coef(c->stream, a));
-  c->launches++;
+  c->launches += G.ndim == 3 ? 2 : 1;
   CU(cudaMemcpyAsync(c->h_scalars, c->d_scalars, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  TRY(ctx_wait(c));
+  TRY(ctx_wait(c, "coefficient setup"));
   if (c->h_scalars[1] & 1) return fail(WP_ENONFINITE, "m or eta holds NaN or Inf");
   if (c->h_scalars[1] & 2) return fail(WP_EINVAL, "m must be > 0 and eta >= 0 everywhere");
   float max_inv_m;
@@ -504,15 +559,7 @@ static int prop_setup(wp_ctx *c, Arena &ar, const Geom &G, const float *m, const
   if (G.ndim == 3) {
     TRY(make_field_maps(&P->b, G));
     TRY(make_field_maps(&P->s, G));
-    const int ntile = G.tiles_x * G.tiles_y;
-    const int slots = c->num_sms * std::max(1, c->occ3d[0][G.R]);
-    int nchunk = std::max(1, slots / ntile);
-    const char *env = getenv("WP_ZCHUNK");
-    int zc = (G.nz + nchunk - 1) / nchunk;
-    if (env && atoi(env) > 0) zc = atoi(env);
-    zc = std::max(zc, std::min(G.nz, 8));
-    P->zchunk = zc;
-    P->grid3 = dim3(G.tiles_x, G.tiles_y, (G.nz + zc - 1) / zc);
+    for (int mode = 0; mode < 2; ++mode) P->plan[mode] = plan3d(G, mode, c->num_sms, c->occ3d[mode][G.R]);
   }
   return WP_OK;
 }
@@ -547,6 +594,10 @@ static int prop_step(Prop &P, const Field3 &u, const Field3 &um, float *out, int
   const Geom &G = P.G;
   TRY(prof_mark(P.c));
   if (G.ndim == 3) {
+    // never hand the kernel a descriptor that was not encoded for its buffer
+    if (!u.mapped || !um.mapped || !P.b.mapped || !P.s.mapped || (uj && !uj->mapped) || (grad && !grad->mapped))
+      return fail(WP_ECUDA, "internal error: a field of the 3D stencil has no TMA descriptor");
+    const Plan3d &pl = P.plan[mode];
     Stencil3dArgs a;
     a.g = G.fg();
     a.c = P.lc;
@@ -554,15 +605,19 @@ static int prop_step(Prop &P, const Field3 &u, const Field3 &um, float *out, int
     a.out = out;
     a.grad = grad ? grad->p : nullptr;
     a.neg_inv_dt2 = P.neg_inv_dt2;
-    a.tflag = P.tflag;
-    a.tiles_x = G.tiles_x;
-    a.tiles_y = G.tiles_y;
-    a.zchunk = P.zchunk;
+    a.tbits = P.tbits;
+    a.nzw = G.nzw;
+    a.tiles_x = pl.tiles_x;
+    a.tiles_y = pl.tiles_y;
+    a.flag_tiles_y = G.tiles_y;
+    a.zchunk = pl.zchunk;
+    a.nzc = pl.nzc;
+    a.nitems = pl.nitems;
     a.err = P.c->d_scalars;
-    CUtensorMap maps[6] = {u.halo, um.tile, P.b.tile, P.s.tile, uj ? uj->tile : P.b.tile,
-                           grad ? grad->tile : P.b.tile};
-    cudaError_t e = mode == kModeAdjGrad ? launch_stencil3d_adj(G.R, P.grid3, P.c->stream, maps, a)
-                                         : launch_stencil3d_fwd(G.R, P.grid3, P.c->stream, maps, a);
+    const CUtensorMap maps[6] = {u.halo[mode], um.tile[mode], P.b.tile[mode], P.s.tile[mode],
+                                 uj ? uj->tile[mode] : P.b.tile[mode], grad ? grad->tile[mode] : P.b.tile[mode]};
+    cudaError_t e = mode == kModeAdjGrad ? launch_stencil3d_adj(G.R, pl.grid, P.c->stream, maps, a)
+                                         : launch_stencil3d_fwd(G.R, pl.grid, P.c->stream, maps, a);
     if (e != cudaSuccess) return fail(WP_ECUDA, "stencil3d launch failed: %s", cudaGetErrorString(e));
   } else {
     Stencil2dArgs a;
@@ -739,7 +794,7 @@ static int do_propagate(wp_ctx *c, const wp_grid *grid, const float *m, const fl
   }
   TRY(run_loop(P, u, G.nt, din, data_d, dsm, n_out ? out_d : nullptr, dir));
   if (host_io && n_out) CU(cudaMemcpyAsync(smp_out, out_d, n_out * 4, cudaMemcpyDeviceToHost, c->stream));
-  return ctx_wait(c);
+  return ctx_wait(c, dir > 0 ? "forward time loop" : "adjoint time loop");
 }
 
 // ---------------------------------------------------------------------------
@@ -832,7 +887,7 @@ static int forward_save(wp_ctx *c, const wp_grid *grid, const float *m, const fl
       if (rec_d) TRY(prop_sample(P, st->drec, prv.p, rec_d, n));
     }
     if (host_io && rec_d) CU(cudaMemcpyAsync(rec_out, rec_d, n_out * 4, cudaMemcpyDeviceToHost, c->stream));
-    TRY(ctx_wait(c));
+    TRY(ctx_wait(c, "forward with snapshots"));
     keep.release_all_to(st->mem);
     return WP_OK;
   }();
@@ -900,7 +955,7 @@ static int backward(wp_state *st, const float *residual, float *grad_out, bool h
   // pitched -> contiguous
   CU(cudaMemcpy2DAsync(grad_out, size_t(G.nx) * 4, g.p, size_t(G.pitch) * 4, size_t(G.nx) * 4,
                        size_t(G.ny) * G.nz, host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
-  return ctx_wait(c);
+  return ctx_wait(c, "backward (recompute, adjoint, gradient)");
 }
 
 // ---------------------------------------------------------------------------
@@ -932,8 +987,8 @@ int wp_create(wp_ctx **out, int device, size_t budget) {
     CU(cudaMemset(c->d_scalars, 0, 64));
     TRY(get_encode());
     for (int R = 1; R <= 8; ++R) {
-      CU(prepare_stencil3d_fwd(R, &c->smem3d[0][R], &c->occ3d[0][R]));
-      CU(prepare_stencil3d_adj(R, &c->smem3d[1][R], &c->occ3d[1][R]));
+      CU(prepare_stencil3d_fwd(R, &c->smem3d[0][R], &c->occ3d[0][R], &c->ty3d[0][R]));
+      CU(prepare_stencil3d_adj(R, &c->smem3d[1][R], &c->occ3d[1][R], &c->ty3d[1][R]));
     }
     return WP_OK;
   }();
@@ -1110,7 +1165,7 @@ int wp_propagate_dev(wp_ctx *c, const wp_grid *grid, const float *m, const float
     TRY(run_loop(P, f, nsteps, none, nullptr, none, nullptr, +1));
     CU(cudaMemcpy2DAsync(u, w, f[nsteps & 1].p, hp, w, rows, cudaMemcpyDeviceToDevice, c->stream));
     CU(cudaMemcpy2DAsync(u_prev, w, f[(nsteps + 1) & 1].p, hp, w, rows, cudaMemcpyDeviceToDevice, c->stream));
-    return ctx_wait(c);
+    return ctx_wait(c, "propagation");
   }();
   return leave(c, stream, rc);
 }
@@ -1201,7 +1256,8 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
 
   // size the work space before touching the device
   Carve cv{nullptr, 0, WP_NOALLOC_MAX_BYTES};
-  auto plan = [&](Carve &c, int **scal, float **b, float **s, float **u0, float **u1, unsigned char **tflag,
+  auto plan = [&](Carve &c, int **scal, float **b, float **s, float **u0, float **u1, unsigned **tbits,
+                  unsigned char **tflag,
                   long long **d_target, int **d_rowptr, int **d_pid, float **d_cw, long long **d_ridx,
                   float **d_rw) {
     *scal = c.take<int>(16);
@@ -1209,6 +1265,7 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
     *s = c.take<float>(G.nfield);
     *u0 = c.take<float>(G.nfield);
     *u1 = c.take<float>(G.nfield);
+    *tbits = G.ndim == 3 ? c.take<unsigned>(size_t(G.tiles_y) * G.tiles_x * G.nzw) : nullptr;
     *tflag = G.ndim == 3 ? c.take<unsigned char>(size_t(G.nz) * G.tiles_y * G.tiles_x) : nullptr;
     *d_target = c.take<long long>(target.size());
     *d_rowptr = c.take<int>(rowptr.size());
@@ -1219,17 +1276,18 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
   };
   int *scal;
   float *b, *s, *u0, *u1, *d_cw, *d_rw;
+  unsigned *tbits;
   unsigned char *tflag;
   long long *d_target, *d_ridx;
   int *d_rowptr, *d_pid;
-  plan(cv, &scal, &b, &s, &u0, &u1, &tflag, &d_target, &d_rowptr, &d_pid, &d_cw, &d_ridx, &d_rw);
+  plan(cv, &scal, &b, &s, &u0, &u1, &tbits, &tflag, &d_target, &d_rowptr, &d_pid, &d_cw, &d_ridx, &d_rw);
   if (cv.over)
     return fail(WP_ENOMEM, "this problem needs %zu bytes of work space; wp_forward_noalloc is limited to %zu",
                 cv.used, size_t(WP_NOALLOC_MAX_BYTES));
   void *base = nullptr;
   TRY(noalloc_scratch(&base));
   Carve c{static_cast<unsigned char *>(base), 0, WP_NOALLOC_MAX_BYTES};
-  plan(c, &scal, &b, &s, &u0, &u1, &tflag, &d_target, &d_rowptr, &d_pid, &d_cw, &d_ridx, &d_rw);
+  plan(c, &scal, &b, &s, &u0, &u1, &tbits, &tflag, &d_target, &d_rowptr, &d_pid, &d_cw, &d_ridx, &d_rw);
 
   // the array keeps the last call's contents: clear what must start at zero
   CU(cudaMemsetAsync(scal, 0, 16 * sizeof(int), st));
@@ -1253,10 +1311,12 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
   ca.b = b;
   ca.s = s;
   ca.tflag = tflag;
+  ca.tbits = tbits;
+  ca.nzw = G.nzw;
   ca.tiles_x = G.tiles_x;
   ca.tiles_y = G.tiles_y;
   ca.tile_w = kTX;
-  ca.tile_h = kTY;
+  ca.tile_h = kTileFlagTY;
   ca.max_inv_m_bits = reinterpret_cast<unsigned int *>(scal + 2);
   ca.bad = scal + 1;
   CU(launch_coef(st, ca));
@@ -1279,22 +1339,20 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
   const float neg_inv_dt2 = static_cast<float>(-1.0 / (G.dt * G.dt));
   float *u[2] = {u0, u1};
   CUtensorMap halo[2], tile[2], tb, ts;
-  dim3 grid3;
-  int zc = 0;
+  Plan3d pl;
   if (G.ndim == 3) {
+    const int ty = stencil3d_tile_y(G.R, kModeFwd);
     for (int i = 0; i < 2; ++i) {
-      TRY(make_map(&halo[i], u[i], G, halo_box_w(G.R), kTY + 2 * G.R));
-      TRY(make_map(&tile[i], u[i], G, kTX, kTY));
+      TRY(make_map(&halo[i], u[i], G, halo_box_w(G.R), ty + 2 * G.R));
+      TRY(make_map(&tile[i], u[i], G, kTX, ty));
     }
-    TRY(make_map(&tb, b, G, kTX, kTY));
-    TRY(make_map(&ts, s, G, kTX, kTY));
-    int smem = 0, occ = 0, dev = 0, nsm = 0;
-    CU(prepare_stencil3d_fwd(G.R, &smem, &occ));
+    TRY(make_map(&tb, b, G, kTX, ty));
+    TRY(make_map(&ts, s, G, kTX, ty));
+    int smem = 0, occ = 0, ty_k = 0, dev = 0, nsm = 0;
+    CU(prepare_stencil3d_fwd(G.R, &smem, &occ, &ty_k));
     CU(cudaGetDevice(&dev));
     CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const int nchunk = std::max(1, nsm * std::max(1, occ) / (G.tiles_x * G.tiles_y));
-    zc = std::max((G.nz + nchunk - 1) / nchunk, std::min(G.nz, 8));
-    grid3 = dim3(G.tiles_x, G.tiles_y, (G.nz + zc - 1) / zc);
+    pl = plan3d(G, kModeFwd, nsm, occ);
   }
   for (int k = 0; k < G.nt; ++k) {
     float *cur = u[k & 1], *prv = u[(k + 1) & 1];
@@ -1306,13 +1364,17 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
       a.out = prv;
       a.grad = nullptr;
       a.neg_inv_dt2 = neg_inv_dt2;
-      a.tflag = tflag;
-      a.tiles_x = G.tiles_x;
-      a.tiles_y = G.tiles_y;
-      a.zchunk = zc;
+      a.tbits = tbits;
+      a.nzw = G.nzw;
+      a.tiles_x = pl.tiles_x;
+      a.tiles_y = pl.tiles_y;
+      a.flag_tiles_y = G.tiles_y;
+      a.zchunk = pl.zchunk;
+      a.nzc = pl.nzc;
+      a.nitems = pl.nitems;
       a.err = scal;
-      CUtensorMap maps[6] = {halo[k & 1], tile[(k + 1) & 1], tb, ts, tb, tb};
-      CU(launch_stencil3d_fwd(G.R, grid3, st, maps, a));
+      const CUtensorMap maps[6] = {halo[k & 1], tile[(k + 1) & 1], tb, ts, tb, tb};
+      CU(launch_stencil3d_fwd(G.R, pl.grid, st, maps, a));
     } else {
       Stencil2dArgs a;
       a.g = G.fg();

@@ -81,7 +81,8 @@ cudaError_t launch_stencil2d(int R, int mode, cudaStream_t st, const Stencil2dAr
 // ---------------------------------------------------------------------------
 // A1: b = dt^2 / (m + eta dt/2) and s = -eta dt / (m + eta dt/2), evaluated in
 // double and stored as float in the pitched layout; per-(plane, tile) damping
-// flags; max(1/m) for the CFL check; non-finite / sign checks of the inputs.
+// flags (bytes, then packed into per-tile z bitmasks by a second kernel);
+// max(1/m) for the CFL check; non-finite / sign checks of the inputs.
 // ---------------------------------------------------------------------------
 __global__ void coef_kernel(const CoefArgs a) {
   const long long nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
@@ -115,12 +116,36 @@ __global__ void coef_kernel(const CoefArgs a) {
   }
 }
 
+// Pack the (plane, tile) damping bytes into one z bitmask per tile:
+// tbits[(ty * tiles_x + tx) * nzw + w] bit b  <=>  tflag[(32 w + b) * tiles_y * tiles_x + ty * tiles_x + tx].
+__global__ void pack_flags_kernel(const CoefArgs a) {
+  const long long nword = static_cast<long long>(a.tiles_y) * a.tiles_x * a.nzw;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < nword;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long tile = i / a.nzw;
+    const int w = static_cast<int>(i - tile * a.nzw);
+    unsigned bits = 0;
+    for (int b = 0; b < 32; ++b) {
+      const long long z = 32ll * w + b;
+      if (z >= a.g.nz) break;
+      if (a.tflag[z * a.tiles_y * a.tiles_x + tile]) bits |= 1u << b;
+    }
+    a.tbits[i] = bits;
+  }
+}
+
 cudaError_t launch_coef(cudaStream_t st, const CoefArgs &a) {
   const long long n = static_cast<long long>(a.g.nx) * a.g.ny * a.g.nz;
   long long blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
   coef_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !a.tbits) return e;
+  const long long nword = static_cast<long long>(a.tiles_y) * a.tiles_x * a.nzw;
+  long long pb = (nword + 255) / 256;
+  if (pb > 152 * 8) pb = 152 * 8;
+  pack_flags_kernel<<<static_cast<unsigned>(pb), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

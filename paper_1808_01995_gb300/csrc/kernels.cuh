@@ -11,14 +11,20 @@ namespace wp {
 struct Stencil3dArgs;
 
 // ---- K1, 3D (stencil3d_fwd.cu / stencil3d_adj.cu) ----
-// maps: u (halo box), u^{n-1}, b, s, u^j, g (the last two only in adjoint mode)
+// maps: u^n (halo'd plane box of the mode), u^{n-1}, b, s, u^j, g (tile boxes of the mode)
 cudaError_t launch_stencil3d_fwd(int R, dim3 grid, cudaStream_t st, const CUtensorMap *maps,
                                  const Stencil3dArgs &a);
 cudaError_t launch_stencil3d_adj(int R, dim3 grid, cudaStream_t st, const CUtensorMap *maps,
                                  const Stencil3dArgs &a);
-// sets the dynamic shared-memory limit and reports the CTA footprint / occupancy
-cudaError_t prepare_stencil3d_fwd(int R, int *smem_bytes, int *blocks_per_sm);
-cudaError_t prepare_stencil3d_adj(int R, int *smem_bytes, int *blocks_per_sm);
+// sets the dynamic shared-memory limit; reports the CTA footprint, occupancy and tile height
+cudaError_t prepare_stencil3d_fwd(int R, int *smem_bytes, int *blocks_per_sm, int *tile_y);
+cudaError_t prepare_stencil3d_adj(int R, int *smem_bytes, int *blocks_per_sm, int *tile_y);
+// tile height (y) of the work tiles of each mode
+int stencil3d_tile_y_fwd(int R);
+int stencil3d_tile_y_adj(int R);
+inline int stencil3d_tile_y(int R, int mode) {
+  return mode == 1 ? stencil3d_tile_y_adj(R) : stencil3d_tile_y_fwd(R);
+}
 
 // ---- K1, 2D (kernels.cu) ----
 struct Stencil2dArgs {
@@ -43,7 +49,9 @@ struct CoefArgs {
   double dt;
   float *b;                // pitched
   float *s;                // pitched
-  unsigned char *tflag;    // 3D only: [nz][tiles_y][tiles_x], pre-zeroed
+  unsigned char *tflag;    // 3D only: [nz][tiles_y][tiles_x] bytes, 1 where eta != 0, pre-zeroed
+  unsigned *tbits;         // 3D only: [tiles_y][tiles_x][nzw] z bitmasks packed from tflag
+  int nzw;
   int tiles_x, tiles_y, tile_w, tile_h;
   unsigned int *max_inv_m_bits;  // float bits of max(1/m), pre-zeroed
   int *bad;                // bit 0: non-finite input, bit 1: m <= 0 or eta < 0

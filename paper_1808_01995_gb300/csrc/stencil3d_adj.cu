@@ -5,22 +5,19 @@
 namespace wp {
 
 template <int R>
-static cudaError_t launch_t(dim3 grid, cudaStream_t st, const CUtensorMap *maps, const Stencil3dArgs &a) {
-  constexpr int bytes = Smem3d<R, kModeAdjGrad>::BYTES;
-  stencil3d_kernel<R, kModeAdjGrad><<<grid, kThreads3d, bytes, st>>>(maps[0], maps[1], maps[2], maps[3], maps[4],
-                                                            maps[5], a);
+static cudaError_t launch_t(dim3 grid, cudaStream_t st, const CUtensorMap *m, const Stencil3dArgs &a) {
+  stencil3d_kernel<R, kModeAdjGrad><<<grid, kThreads3d, Cfg3d<R, kModeAdjGrad>::SMEM, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], a);
   return cudaGetLastError();
 }
 
 template <int R>
-static cudaError_t prepare_t(int *smem_bytes, int *blocks_per_sm) {
-  constexpr int bytes = Smem3d<R, kModeAdjGrad>::BYTES;
-  cudaError_t e = cudaFuncSetAttribute(stencil3d_kernel<R, kModeAdjGrad>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+static cudaError_t prepare_t(int *smem_bytes, int *blocks_per_sm, int *tile_y) {
+  constexpr int bytes = Cfg3d<R, kModeAdjGrad>::SMEM;
+  cudaError_t e = cudaFuncSetAttribute(stencil3d_kernel<R, kModeAdjGrad>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
   *smem_bytes = bytes;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, stencil3d_kernel<R, kModeAdjGrad>,
-                                                       kThreads3d, bytes);
+  *tile_y = Cfg3d<R, kModeAdjGrad>::TY;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, stencil3d_kernel<R, kModeAdjGrad>, kThreads3d, bytes);
 }
 
 #define WP_DISPATCH(F, ...)                 \
@@ -41,8 +38,27 @@ cudaError_t launch_stencil3d_adj(int R, dim3 grid, cudaStream_t st, const CUtens
   WP_DISPATCH(launch_t, grid, st, maps, a)
 }
 
-cudaError_t prepare_stencil3d_adj(int R, int *smem_bytes, int *blocks_per_sm) {
-  WP_DISPATCH(prepare_t, smem_bytes, blocks_per_sm)
+template <int R>
+static int tile_y_t() {
+  return Cfg3d<R, kModeAdjGrad>::TY;
+}
+
+int stencil3d_tile_y_adj(int R) {
+  switch (R) {
+    case 1: return tile_y_t<1>();
+    case 2: return tile_y_t<2>();
+    case 3: return tile_y_t<3>();
+    case 4: return tile_y_t<4>();
+    case 5: return tile_y_t<5>();
+    case 6: return tile_y_t<6>();
+    case 7: return tile_y_t<7>();
+    case 8: return tile_y_t<8>();
+    default: return 16;
+  }
+}
+
+cudaError_t prepare_stencil3d_adj(int R, int *smem_bytes, int *blocks_per_sm, int *tile_y) {
+  WP_DISPATCH(prepare_t, smem_bytes, blocks_per_sm, tile_y)
 }
 
 }  // namespace wp
