@@ -172,10 +172,11 @@ size_t wp_bytes_in_use(const wp_ctx *ctx);
 /* Number of kernels this context has launched (graph replays count every node). */
 uint64_t wp_kernel_launches(const wp_ctx *ctx);
 
-/* Profiling: while enabled, every stencil (K1) launch is bracketed by CUDA events
- * on the context's stream; wp_profile_read returns the summed device time (ms)
- * and the number of bracketed launches since the last reset. */
-int wp_set_profiling(wp_ctx *ctx, int enabled);
+/* Profiling: with every = N > 0, every N-th stencil (K1) launch is bracketed by
+ * CUDA events on the context's stream (0 turns it off); wp_profile_read returns
+ * the summed device time (ms) of the bracketed launches and their number since
+ * the last reset.  Sampling (N > 1) keeps the event nodes out of most steps. */
+int wp_set_profiling(wp_ctx *ctx, int every);
 int wp_profile_read(wp_ctx *ctx, double *stencil_ms, uint64_t *stencil_launches, int reset);
 
 /* ---- forward modelling without any device allocation -----------------------

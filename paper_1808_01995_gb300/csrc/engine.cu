@@ -71,13 +71,43 @@ struct wp_ctx {
   int occ3d[2][9] = {};
   int ty3d[2][9] = {};
   bool broken = false;
-  // profiling: an event pair around every stencil launch, summed on read
+  // profiling: an event pair around every prof_every-th stencil launch, summed on read
   bool profiling = false;
+  int prof_every = 1;
+  uint64_t prof_seq = 0;  // stencil launches seen (restarts for every graph hash/capture pass)
+  bool prof_open = false; // the last stencil launch was bracketed
   std::vector<cudaEvent_t> prof_events;   // 2 per launch
   size_t prof_used = 0;
   double prof_ms = 0.0;
   uint64_t prof_count = 0;
+  std::vector<cudaEvent_t> *prof_ev = nullptr;  // where the next stencil events go
+  size_t *prof_n = nullptr;
+  // CUDA graphs of time-loop blocks (see graph_replay)
+  bool use_graphs = true;
+  bool hashing = false, capturing = false;
+  uint64_t hash = 0;
+  size_t hash_marks = 0;
+  long long *d_rows = nullptr;            // device row bases read by the sparse kernels
+  std::vector<struct GraphEntry *> graphs;
+  uint64_t graph_stamp = 0;
 };
+
+// One instantiated graph of a block of time steps, replayable while every
+// kernel argument (hashed into `key`) is unchanged.
+struct GraphEntry {
+  uint64_t key = 0;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaEvent_t> ev;  // events recorded by the graph's profiling nodes
+  size_t nev = 0;
+  uint64_t kernels = 0;         // kernel nodes per replay
+  uint64_t stamp = 0;
+};
+
+static void graph_destroy(GraphEntry *e) {
+  if (e->exec) cudaGraphExecDestroy(e->exec);
+  for (cudaEvent_t ev : e->ev) cudaEventDestroy(ev);
+  delete e;
+}
 
 static size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -566,39 +596,83 @@ static int prop_setup(wp_ctx *c, Arena &ar, const Geom &G, const float *m, const
 
 // One stencil step: out = update(u, um) (out may alias um).  Adjoint+gradient
 // mode also accumulates into grad using the forward field uj.
+// While c->hashing is set the launch helpers fold their complete kernel
+// arguments (TMA descriptors included) into c->hash instead of launching: two
+// blocks of work with the same hash enqueue identical kernels.
+static void hash_bytes(wp_ctx *c, const void *p, size_t n) {
+  const unsigned char *b = static_cast<const unsigned char *>(p);
+  uint64_t h = c->hash;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  c->hash = h;
+}
+
 static int prof_mark(wp_ctx *c) {
   if (!c->profiling) return WP_OK;
-  if (c->prof_used == c->prof_events.size()) {
+  if (c->hashing) {
+    c->hash_marks++;
+    return WP_OK;
+  }
+  std::vector<cudaEvent_t> &ev = *c->prof_ev;
+  size_t &n = *c->prof_n;
+  if (n == ev.size()) {
     cudaEvent_t e;
     CU(cudaEventCreate(&e));
-    c->prof_events.push_back(e);
+    ev.push_back(e);
   }
-  CU(cudaEventRecord(c->prof_events[c->prof_used++], c->stream));
+  // inside a capture only an "external" record becomes a graph node the host can time
+  if (c->capturing) CU(cudaEventRecordWithFlags(ev[n++], c->stream, cudaEventRecordExternal));
+  else CU(cudaEventRecord(ev[n++], c->stream));
   return WP_OK;
 }
 
-// Fold the recorded stencil intervals into the totals (the stream must be idle).
-static int prof_collect(wp_ctx *c) {
-  for (size_t i = 0; i + 1 < c->prof_used; i += 2) {
+// Fold recorded (start, end) event pairs into the totals (the events must have completed).
+static int prof_fold(wp_ctx *c, const std::vector<cudaEvent_t> &ev, size_t n) {
+  for (size_t i = 0; i + 1 < n; i += 2) {
     float ms = 0.f;
-    CU(cudaEventElapsedTime(&ms, c->prof_events[i], c->prof_events[i + 1]));
+    CU(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
     c->prof_ms += ms;
     c->prof_count++;
   }
+  return WP_OK;
+}
+
+static int prof_collect(wp_ctx *c) {
+  TRY(prof_fold(c, c->prof_events, c->prof_used));
   c->prof_used = 0;
   return WP_OK;
+}
+
+// Wait (with the context deadline) for one event.
+static int wait_event(wp_ctx *c, cudaEvent_t ev, const char *what) {
+  const auto t0 = std::chrono::steady_clock::now();
+  int spins = 0;
+  while (true) {
+    cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return WP_OK;
+    if (e != cudaErrorNotReady) return fail(WP_ECUDA, "%s failed: %s", what, cudaGetErrorString(e));
+    if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > c->timeout_s) {
+      c->broken = true;
+      return fail(WP_ETIMEOUT, "%s did not finish within %.1f s", what, c->timeout_s);
+    }
+    if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(spins > 1000 ? 200 : 20));
+  }
 }
 
 static int prop_step(Prop &P, const Field3 &u, const Field3 &um, float *out, int mode, const Field3 *uj,
                      const Field3 *grad) {
   const Geom &G = P.G;
-  TRY(prof_mark(P.c));
+  P.c->prof_open = P.c->profiling && (P.c->prof_seq++ % uint64_t(P.c->prof_every)) == 0;
+  if (P.c->prof_open) TRY(prof_mark(P.c));
   if (G.ndim == 3) {
     // never hand the kernel a descriptor that was not encoded for its buffer
     if (!u.mapped || !um.mapped || !P.b.mapped || !P.s.mapped || (uj && !uj->mapped) || (grad && !grad->mapped))
       return fail(WP_ECUDA, "internal error: a field of the 3D stencil has no TMA descriptor");
     const Plan3d &pl = P.plan[mode];
     Stencil3dArgs a;
+    memset(&a, 0, sizeof a);
     a.g = G.fg();
     a.c = P.lc;
     a.u = u.p;
@@ -616,11 +690,19 @@ static int prop_step(Prop &P, const Field3 &u, const Field3 &um, float *out, int
     a.err = P.c->d_scalars;
     const CUtensorMap maps[6] = {u.halo[mode], um.tile[mode], P.b.tile[mode], P.s.tile[mode],
                                  uj ? uj->tile[mode] : P.b.tile[mode], grad ? grad->tile[mode] : P.b.tile[mode]};
+    if (P.c->hashing) {
+      hash_bytes(P.c, &mode, sizeof mode);
+      hash_bytes(P.c, &a, sizeof a);
+      hash_bytes(P.c, maps, sizeof maps);
+      hash_bytes(P.c, &pl.grid, sizeof pl.grid);
+      return P.c->prof_open ? prof_mark(P.c) : WP_OK;
+    }
     cudaError_t e = mode == kModeAdjGrad ? launch_stencil3d_adj(G.R, pl.grid, P.c->stream, maps, a)
                                          : launch_stencil3d_fwd(G.R, pl.grid, P.c->stream, maps, a);
     if (e != cudaSuccess) return fail(WP_ECUDA, "stencil3d launch failed: %s", cudaGetErrorString(e));
   } else {
     Stencil2dArgs a;
+    memset(&a, 0, sizeof a);
     a.g = G.fg();
     a.c = P.lc;
     a.u = u.p;
@@ -631,12 +713,17 @@ static int prop_step(Prop &P, const Field3 &u, const Field3 &um, float *out, int
     a.grad = grad ? grad->p : nullptr;
     a.uj = uj ? uj->p : nullptr;
     a.neg_inv_dt2 = P.neg_inv_dt2;
+    if (P.c->hashing) {
+      hash_bytes(P.c, &mode, sizeof mode);
+      hash_bytes(P.c, &a, sizeof a);
+      return P.c->prof_open ? prof_mark(P.c) : WP_OK;
+    }
     cudaError_t e = launch_stencil2d(G.R, mode, P.c->stream, a);
     if (e != cudaSuccess) return fail(WP_ECUDA, "stencil2d launch failed: %s", cudaGetErrorString(e));
   }
   P.c->launches++;
-  TRY(prof_mark(P.c));
-  if (P.c->prof_used >= 4096) {  // bound the event pool: fold what has completed
+  if (P.c->prof_open) TRY(prof_mark(P.c));
+  if (!P.c->capturing && P.c->prof_used >= 4096) {  // bound the event pool: fold what has completed
     TRY(ctx_wait(P.c));
     TRY(prof_collect(P.c));
   }
@@ -644,9 +731,10 @@ static int prop_step(Prop &P, const Field3 &u, const Field3 &um, float *out, int
 }
 
 static int prop_inject(Prop &P, const DevPoints &dp, const float *data, long long row, float *u, float *grad,
-                       const float *uj) {
+                       const float *uj, const long long *row_base = nullptr) {
   if (dp.ntarget == 0) return WP_OK;
   InjectArgs a;
+  memset(&a, 0, sizeof a);
   a.ntarget = dp.ntarget;
   a.target = dp.target;
   a.rowptr = dp.rowptr;
@@ -654,30 +742,145 @@ static int prop_inject(Prop &P, const DevPoints &dp, const float *data, long lon
   a.w = dp.cw;
   a.data = data;
   a.npts = dp.npts;
+  a.row_base = row_base;
   a.row = row;
   a.u = u;
   a.b = P.b.p;
   a.grad = grad;
   a.uj = uj;
   a.neg_inv_dt2 = P.neg_inv_dt2;
+  if (P.c->hashing) {
+    hash_bytes(P.c, &a, sizeof a);
+    return WP_OK;
+  }
   CU(launch_inject(P.c->stream, a));
   P.c->launches++;
   return WP_OK;
 }
 
-static int prop_sample(Prop &P, const DevPoints &dp, const float *u, float *out, long long row) {
+static int prop_sample(Prop &P, const DevPoints &dp, const float *u, float *out, long long row,
+                       const long long *row_base = nullptr) {
   if (dp.npts == 0) return WP_OK;
   InterpArgs a;
+  memset(&a, 0, sizeof a);
   a.npts = dp.npts;
   a.ncorner = dp.nc;
   a.idx = dp.idx;
   a.w = dp.w;
   a.u = u;
   a.out = out;
+  a.row_base = row_base;
   a.row = row;
+  if (P.c->hashing) {
+    hash_bytes(P.c, &a, sizeof a);
+    return WP_OK;
+  }
   CU(launch_interp(P.c->stream, a));
   P.c->launches++;
   return WP_OK;
+}
+
+static int prop_add_row(wp_ctx *c, long long *p, long long d) {
+  if (c->hashing) {
+    hash_bytes(c, &p, sizeof p);
+    hash_bytes(c, &d, sizeof d);
+    return WP_OK;
+  }
+  CU(launch_add_row(c->stream, p, d));
+  c->launches++;
+  return WP_OK;
+}
+
+// Run `block` (a callable that enqueues one block of work through the helpers
+// above) `replays` times as a cached CUDA graph.  The block is first run in
+// hashing mode; a cached graph with the same hash is replayed, otherwise the
+// block is captured and instantiated (at most 16 graphs per context, least
+// recently used evicted).  With profiling on, the stencil event pairs inside the
+// graph are folded after every replay.
+template <class F>
+static int graph_replay(wp_ctx *c, F &&block, int replays) {
+  if (replays <= 0) return WP_OK;
+  c->hashing = true;
+  c->hash = 1469598103934665603ull ^ (c->profiling ? 0x9e3779b97f4a7c15ull : 0ull);
+  c->hash_marks = 0;
+  const uint64_t seq0 = c->prof_seq;
+  c->prof_seq = 0;
+  int rc = block();
+  c->hashing = false;
+  TRY(rc);
+  const uint64_t key = c->hash;
+  GraphEntry *e = nullptr;
+  for (GraphEntry *g : c->graphs)
+    if (g->key == key) e = g;
+  if (!e) {
+    e = new GraphEntry();
+    e->key = key;
+    for (size_t i = 0; i < c->hash_marks; ++i) {  // events exist before capture starts
+      cudaEvent_t ev;
+      if (cudaEventCreate(&ev) != cudaSuccess) {
+        graph_destroy(e);
+        return fail(WP_ECUDA, "cudaEventCreate failed");
+      }
+      e->ev.push_back(ev);
+    }
+    std::vector<cudaEvent_t> *sev = c->prof_ev;
+    size_t *sn = c->prof_n;
+    c->prof_ev = &e->ev;
+    c->prof_n = &e->nev;
+    const uint64_t l0 = c->launches;
+    c->capturing = true;
+    cudaGraph_t g = nullptr;
+    c->prof_seq = 0;
+    cudaError_t be = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    int brc = be == cudaSuccess ? block() : WP_OK;
+    cudaError_t ee = be == cudaSuccess ? cudaStreamEndCapture(c->stream, &g) : be;
+    c->capturing = false;
+    c->prof_ev = sev;
+    c->prof_n = sn;
+    e->kernels = c->launches - l0;
+    c->launches = l0;
+    cudaError_t ie = cudaSuccess;
+    if (brc == WP_OK && ee == cudaSuccess) ie = cudaGraphInstantiate(&e->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (brc != WP_OK || ee != cudaSuccess || ie != cudaSuccess) {
+      graph_destroy(e);
+      if (brc != WP_OK) return brc;
+      return fail(WP_ECUDA, "graph capture failed: %s", cudaGetErrorString(ee != cudaSuccess ? ee : ie));
+    }
+    if (c->graphs.size() >= 16) {
+      auto it = std::min_element(c->graphs.begin(), c->graphs.end(),
+                                 [](GraphEntry *x, GraphEntry *y) { return x->stamp < y->stamp; });
+      graph_destroy(*it);
+      c->graphs.erase(it);
+    }
+    c->graphs.push_back(e);
+  }
+  c->prof_seq = seq0;
+  e->stamp = ++c->graph_stamp;
+  for (int r = 0; r < replays; ++r) {
+    CU(cudaGraphLaunch(e->exec, c->stream));
+    c->launches += e->kernels;
+    if (c->profiling && e->nev) {
+      TRY(wait_event(c, e->ev[e->nev - 1], "graph replay"));
+      TRY(prof_fold(c, e->ev, e->nev));
+    }
+  }
+  return WP_OK;
+}
+
+// Steps per graph replay: an even block of 8..64 steps leaving the smallest
+// remainder (0 for loops too short to be worth a graph).
+static int graph_block(wp_ctx *c, int nt) {
+  if (!c->use_graphs || nt < 16) return 0;
+  int best = 0, best_rem = nt;
+  for (int B = 64; B >= 8; B -= 2) {
+    const int rem = nt % B;
+    if (rem < best_rem) {
+      best = B;
+      best_rem = rem;
+    }
+  }
+  return best;
 }
 
 static int alloc_field(Arena &ar, const Geom &G, Field3 *f, bool zero, cudaStream_t st) {
@@ -689,10 +892,31 @@ static int alloc_field(Arena &ar, const Geom &G, Field3 *f, bool zero, cudaStrea
 
 // Time loop shared by forward and adjoint: for k = 0..nt-1 one update, inject
 // data row (dir > 0 ? k : nt-1-k) at `inj`, sample `smp` into the same row of
-// `out`.  u[k & 1] holds the current level before step k.
+// `out`.  u[k & 1] holds the current level before step k.  Full blocks of B
+// steps run as replays of one CUDA graph (B even, so buffer parity repeats);
+// the sparse kernels take their row from a device base the graph advances.
 static int run_loop(Prop &P, Field3 u[2], int nt, const DevPoints &inj, const float *data, const DevPoints &smp,
                     float *out, int dir) {
-  for (int k = 0; k < nt; ++k) {
+  wp_ctx *c = P.c;
+  int k0 = 0;
+  const int B = graph_block(c, nt);
+  if (B > 0) {
+    long long *rb = c->d_rows;
+    CU(launch_set_row(c->stream, rb, dir > 0 ? 0 : nt - 1));
+    c->launches++;
+    auto block = [&]() -> int {
+      for (int j = 0; j < B; ++j) {
+        Field3 &cur = u[j & 1], &prv = u[(j + 1) & 1];
+        TRY(prop_step(P, cur, prv, prv.p, kModeFwd, nullptr, nullptr));
+        TRY(prop_inject(P, inj, data, dir * j, prv.p, nullptr, nullptr, rb));
+        if (out) TRY(prop_sample(P, smp, prv.p, out, dir * j, rb));
+      }
+      return prop_add_row(c, rb, static_cast<long long>(dir) * B);
+    };
+    TRY(graph_replay(c, block, nt / B));
+    k0 = (nt / B) * B;
+  }
+  for (int k = k0; k < nt; ++k) {
     const long long row = dir > 0 ? k : nt - 1 - k;
     Field3 &cur = u[k & 1], &prv = u[(k + 1) & 1];
     TRY(prop_step(P, cur, prv, prv.p, kModeFwd, nullptr, nullptr));
@@ -983,6 +1207,11 @@ int wp_create(wp_ctx **out, int device, size_t budget) {
     CU(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming));
     CU(cudaMalloc(&c->d_scalars, 64));
+    CU(cudaMalloc(&c->d_rows, 64));
+    c->prof_ev = &c->prof_events;
+    c->prof_n = &c->prof_used;
+    const char *ng = getenv("WP_NO_GRAPHS");
+    c->use_graphs = !(ng && atoi(ng) != 0);
     CU(cudaMallocHost(&c->h_scalars, 64));
     CU(cudaMemset(c->d_scalars, 0, 64));
     TRY(get_encode());
@@ -1009,6 +1238,8 @@ void wp_destroy(wp_ctx *c) {
   if (c->d_scalars) cudaFree(c->d_scalars);
   if (c->h_scalars) cudaFreeHost(c->h_scalars);
   for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
+  for (GraphEntry *g : c->graphs) graph_destroy(g);
+  if (c->d_rows) cudaFree(c->d_rows);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_done) cudaEventDestroy(c->ev_done);
   if (c->stream) cudaStreamDestroy(c->stream);
@@ -1023,9 +1254,12 @@ int wp_set_timeout(wp_ctx *c, double seconds) {
 
 size_t wp_bytes_in_use(const wp_ctx *c) { return c ? c->in_use : 0; }
 
-int wp_set_profiling(wp_ctx *c, int enabled) {
+int wp_set_profiling(wp_ctx *c, int every) {
   if (!c) return fail(WP_EINVAL, "context is NULL");
-  c->profiling = enabled != 0;
+  if (every < 0) return fail(WP_EINVAL, "every must be >= 0");
+  c->profiling = every > 0;
+  c->prof_every = every > 0 ? every : 1;
+  c->prof_seq = 0;
   c->prof_used = 0;
   return WP_OK;
 }
@@ -1358,6 +1592,7 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
     float *cur = u[k & 1], *prv = u[(k + 1) & 1];
     if (G.ndim == 3) {
       Stencil3dArgs a;
+      memset(&a, 0, sizeof a);
       a.g = G.fg();
       a.c = lc;
       a.u = cur;
@@ -1377,6 +1612,7 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
       CU(launch_stencil3d_fwd(G.R, pl.grid, st, maps, a));
     } else {
       Stencil2dArgs a;
+      memset(&a, 0, sizeof a);
       a.g = G.fg();
       a.c = lc;
       a.u = cur;
@@ -1391,6 +1627,8 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
     }
     if (!target.empty()) {
       InjectArgs ia;
+      memset(&ia, 0, sizeof ia);
+      ia.row_base = nullptr;
       ia.ntarget = int(target.size());
       ia.target = d_target;
       ia.rowptr = d_rowptr;
@@ -1408,6 +1646,8 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
     }
     if (nrec > 0) {
       InterpArgs pa;
+      memset(&pa, 0, sizeof pa);
+      pa.row_base = nullptr;
       pa.npts = nrec;
       pa.ncorner = pr.nc;
       pa.idx = d_ridx;

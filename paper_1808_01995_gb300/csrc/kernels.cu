@@ -174,7 +174,8 @@ cudaError_t launch_check_finite(cudaStream_t st, const float *x, long long n, in
 __global__ void inject_kernel(const InjectArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.ntarget) return;
-  const float *q = a.data + a.row * a.npts;
+  const long long row = a.row + (a.row_base ? *a.row_base : 0);
+  const float *q = a.data + row * a.npts;
   float acc = 0.f;
   for (int k = a.rowptr[i]; k < a.rowptr[i + 1]; ++k) acc = fmaf(a.w[k], q[a.pid[k]], acc);
   const long long t = a.target[i];
@@ -198,12 +199,26 @@ __global__ void interp_kernel(const InterpArgs a) {
     const long long k = static_cast<long long>(i) * a.ncorner + c;
     acc = fmaf(a.w[k], a.u[a.idx[k]], acc);
   }
-  a.out[a.row * a.npts + i] = acc;
+  const long long row = a.row + (a.row_base ? *a.row_base : 0);
+  a.out[row * a.npts + i] = acc;
 }
 
 cudaError_t launch_interp(cudaStream_t st, const InterpArgs &a) {
   if (a.npts <= 0) return cudaSuccess;
   interp_kernel<<<(a.npts + 127) / 128, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+__global__ void set_row_kernel(long long *p, long long v) { *p = v; }
+__global__ void add_row_kernel(long long *p, long long d) { *p += d; }
+
+cudaError_t launch_set_row(cudaStream_t st, long long *p, long long v) {
+  set_row_kernel<<<1, 1, 0, st>>>(p, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_row(cudaStream_t st, long long *p, long long d) {
+  add_row_kernel<<<1, 1, 0, st>>>(p, d);
   return cudaGetLastError();
 }
 

@@ -67,7 +67,8 @@ struct InjectArgs {
   const float *w;            // weight of each entry
   const float *data;         // [nt][npts]
   int npts;
-  long long row;             // time row of `data`
+  const long long *row_base; // optional device row base (graph replays); row is added to it
+  long long row;             // time row of `data` (offset from *row_base if set)
   float *u;                  // field receiving dt^2/(m + eta dt/2) * sum w q
   const float *b;
   float *grad;               // optional: gradient correction at the targets
@@ -84,9 +85,14 @@ struct InterpArgs {
   const float *w;            // [npts][ncorner]
   const float *u;
   float *out;                // [nt][npts]
+  const long long *row_base; // optional device row base (graph replays); row is added to it
   long long row;
 };
 cudaError_t launch_interp(cudaStream_t st, const InterpArgs &a);
+
+// *p = v / *p += d (row bases of graph replays), one thread
+cudaError_t launch_set_row(cudaStream_t st, long long *p, long long v);
+cudaError_t launch_add_row(cudaStream_t st, long long *p, long long d);
 
 // ---- misc ----
 // bit 0 of *bad set if any of x[0..n) is NaN or Inf

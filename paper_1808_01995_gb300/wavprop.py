@@ -200,8 +200,9 @@ def wp_kernel_launches(ctx: int) -> int:
     return int(lib().wp_kernel_launches(ctx))
 
 
-def wp_set_profiling(ctx: int, enabled: bool) -> None:
-    _check(lib().wp_set_profiling(ctx, 1 if enabled else 0))
+def wp_set_profiling(ctx: int, every: int) -> None:
+    """Bracket every ``every``-th stencil launch with CUDA events (0: off)."""
+    _check(lib().wp_set_profiling(ctx, int(every)))
 
 
 def wp_profile_read(ctx: int, reset: bool = True):
