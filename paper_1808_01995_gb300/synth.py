@@ -174,7 +174,12 @@ def layers_3d(space_order: int = 8, n: int = 256, h: float = 10.0, nbl: int = 40
 
 
 def _gaussian_smooth(v: np.ndarray, sigma: float) -> np.ndarray:
-    """Separable Gaussian smoothing with edge replication (pure numpy)."""
+    """Separable Gaussian smoothing with edge replication, truncated at 3 sigma."""
+    try:
+        from scipy.ndimage import gaussian_filter
+        return gaussian_filter(v.astype(np.float64), sigma, mode="nearest", truncate=3.0)
+    except ImportError:
+        pass
     rad = int(math.ceil(3.0 * sigma))
     t = np.arange(-rad, rad + 1, dtype=np.float64)
     ker = np.exp(-0.5 * (t / sigma) ** 2)
