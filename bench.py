@@ -51,6 +51,11 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--serving", type=int, default=24,
+                   help="requests of the shot-serving stream (0 skips the serving leg)")
+    p.add_argument("--serving-slots", type=int, default=4)
+    p.add_argument("--serving-scale", type=float, default=1.0,
+                   help="scale of the request sizes and nt (1.0 = 128..320 x 128..320 x 128..200 + 40, nt 500..2000)")
     p.add_argument("--profile-every", type=int, default=10,
                    help="bracket every N-th stencil launch with CUDA events in the timed region")
     return p.parse_args()
@@ -252,6 +257,62 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def serving_leg(args):
+    """Shot-serving stream: Poisson arrivals at 1.25x the sequential service rate,
+    served by ShotServer (continuous batching) and, for comparison, one request
+    at a time with a fresh context each (plain calls)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_1808_01995_gb300 import serving as S
+    from paper_1808_01995_gb300 import synth
+    specs = synth.serving_requests(count=args.serving, size_scale=args.serving_scale)
+    with ThreadPoolExecutor(8) as ex:
+        base = list(ex.map(S.make_request, specs))
+
+    def fresh():
+        out = []
+        for r in base:
+            c = S.ShotRequest(id=r.id, kind=r.kind, grid=r.grid, m=r.m, eta=r.eta, wavelet=r.wavelet, src=r.src,
+                              rec=r.rec, d_obs=r.d_obs, snap_interval=r.snap_interval)
+            out.append(c)
+        return out
+
+    # calibration: sequential service times (also warms the caches)
+    import time as _t
+    from paper_1808_01995_gb300 import wavprop as W
+    service = []
+    for r in fresh():
+        t0 = _t.perf_counter()
+        with W.Context(0) as c:
+            S.run_request(c.handle, r)
+        service.append(_t.perf_counter() - t0)
+    mu = 1.0 / float(np.mean(service))
+    rate = 1.25 * mu
+    arrivals = S.poisson_arrivals(len(base), rate, seed=1808 + 4)
+    plain = S.serve_sequential_plain(fresh(), arrivals)
+    served = S.serve_stream(fresh(), arrivals, slots=args.serving_slots)
+    # capacity: the whole stream queued at t = 0
+    burst = np.zeros(len(base))
+    plain_sat = S.serve_sequential_plain(fresh(), burst)
+    served_sat = S.serve_stream(fresh(), burst, slots=args.serving_slots)
+    kinds = [s["kind"] for s in specs]
+    return {"requests": len(base), "forward": kinds.count("forward"), "gradient": kinds.count("gradient"),
+            "arrival_rate_per_s": rate, "sequential_service_rate_per_s": mu,
+            "mean_service_s": float(np.mean(service)),
+            "size_scale": args.serving_scale,
+            "served": served, "plain": plain,
+            "p99_speedup": (plain["p99_latency_s"] / served["p99_latency_s"]
+                            if served["p99_latency_s"] else None),
+            "shots_per_hour_ratio": (served["shots_per_hour"] / plain["shots_per_hour"]
+                                     if plain["shots_per_hour"] else None),
+            "capacity": {"served_shots_per_hour": served_sat["shots_per_hour"],
+                         "plain_shots_per_hour": plain_sat["shots_per_hour"],
+                         "served_p99_s": served_sat["p99_latency_s"], "plain_p99_s": plain_sat["p99_latency_s"],
+                         "served_errors": served_sat["errors"], "plain_errors": plain_sat["errors"],
+                         "ratio": (served_sat["shots_per_hour"] / plain_sat["shots_per_hour"]
+                                   if plain_sat["shots_per_hour"] else None)}}
+
+
 def run_ours(args):
     world, rank, local = dist_init()
     import torch
@@ -346,6 +407,10 @@ def run_ours(args):
                "d2h_bytes_per_step": int(out_h.nbytes), "steps": ke,
                "call": "wp_forward (host arrays, pinned)"}
 
+    serving = None
+    if args.serving > 0 and rank == 0:
+        serving = serving_leg(args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, steps, el, nthreads = oracle_sample(model, dt, args.cpu_seconds)
@@ -357,7 +422,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": describe(model, nt, dt),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clk.summary()}
+                "clocks": clk.summary(), "serving": serving}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

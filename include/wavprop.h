@@ -151,6 +151,27 @@ int wp_gradient_dev(wp_ctx *ctx, const wp_grid *grid, const float *m, const floa
 int wp_propagate_dev(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *eta,
                      float *u_prev, float *u, int nsteps, void *stream);
 
+/* FWI objective and gradient of one shot (Eq. AS, Eq. Grad; the per-source
+ * function of Sec. 3.4): forward with snapshots, residual r = d - d_obs,
+ * *misfit = 1/2 ||r||^2 (summed in double, deterministic order), and
+ * grad_out = J^T r.  d_obs[nt][nrec]; the _dev variant takes device arrays. */
+int wp_fwi_gradient(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *eta,
+                    const float *wavelet, int nsrc, const double *src_coords, const float *d_obs,
+                    int nrec, const double *rec_coords, int snap_interval, float *grad_out,
+                    double *misfit);
+int wp_fwi_gradient_dev(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *eta,
+                        const float *wavelet, int nsrc, const double *src_coords,
+                        const float *d_obs, int nrec, const double *rec_coords, int snap_interval,
+                        float *grad_out, double *misfit, void *stream);
+
+/* Release cached (not live) device blocks of the context until it holds at most
+ * keep_bytes.  Waits for the context's stream first. */
+int wp_trim(wp_ctx *ctx, size_t keep_bytes);
+
+/* Change the context's device-memory budget (later allocations release cached
+ * blocks first and fail with WP_ENOMEM beyond it). */
+int wp_set_budget(wp_ctx *ctx, size_t hbm_budget_bytes);
+
 /* ---- split forward / backward (autograd, serving) ---------------------------
  * wp_forward_save runs the forward (device arrays) and keeps its snapshots
  * resident in *state; wp_backward(state, residual, grad) then returns

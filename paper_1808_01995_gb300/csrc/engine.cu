@@ -111,10 +111,13 @@ static void graph_destroy(GraphEntry *e) {
 
 static size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Device blocks are stream-ordered allocations on the context's stream, so
+// releasing them never waits for work of other contexts (cudaFree would
+// synchronise the whole device).
 static void release_cache(wp_ctx *c, size_t need) {
   while (!c->cache.empty() && (need == 0 || c->in_use + need > c->budget)) {
     auto it = std::prev(c->cache.end());
-    cudaFree(it->second);
+    cudaFreeAsync(it->second, c->stream);
     c->in_use -= it->first;
     c->cache.erase(it);
   }
@@ -123,7 +126,7 @@ static void release_cache(wp_ctx *c, size_t need) {
 static int dev_alloc(wp_ctx *c, size_t bytes, void **out) {
   bytes = round_up(std::max<size_t>(bytes, 1), 256);
   auto it = c->cache.lower_bound(bytes);
-  if (it != c->cache.end() && it->first <= 2 * bytes) {
+  if (it != c->cache.end() && it->first <= bytes + bytes / 4) {  // reuse a block at most 25 % larger
     *out = it->second;
     c->live[*out] = it->first;
     c->cache.erase(it);
@@ -133,16 +136,17 @@ static int dev_alloc(wp_ctx *c, size_t bytes, void **out) {
   if (c->in_use + bytes > c->budget)
     return fail(WP_ENOMEM, "request of %zu bytes exceeds the context budget (%zu of %zu bytes in use)",
                 bytes, c->in_use, c->budget);
-  cudaError_t e = cudaMalloc(out, bytes);
+  cudaError_t e = cudaMallocAsync(out, bytes, c->stream);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
     release_cache(c, 0);
-    e = cudaMalloc(out, bytes);
+    cudaStreamSynchronize(c->stream);
+    e = cudaMallocAsync(out, bytes, c->stream);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
     *out = nullptr;
-    return fail(e == cudaErrorMemoryAllocation ? WP_ENOMEM : WP_ECUDA, "cudaMalloc(%zu) failed: %s", bytes,
+    return fail(e == cudaErrorMemoryAllocation ? WP_ENOMEM : WP_ECUDA, "cudaMallocAsync(%zu) failed: %s", bytes,
                 cudaGetErrorString(e));
   }
   c->in_use += bytes;
@@ -1042,9 +1046,11 @@ static void state_release(wp_state *st) {
   st->mem.clear();
 }
 
+// host_in: m, eta and the wavelet are host arrays; host_rec: rec_out is a host array.
 static int forward_save(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *wavelet,
                         int nsrc, const double *src_xyz, int nrec, const double *rec_xyz, int snap_interval,
-                        float *rec_out, bool host_io, wp_state **out) {
+                        float *rec_out, bool host_in, bool host_rec, wp_state **out) {
+  const bool host_io = host_in;
   *out = nullptr;
   wp_state *st = new wp_state();
   st->c = c;
@@ -1095,7 +1101,7 @@ static int forward_save(wp_ctx *c, const wp_grid *grid, const float *m, const fl
     if (st->nseg > 0) TRY(keep.alloc(&st->snaps, size_t(st->nseg) * 2 * G.nfield));
     float *rec_d = nullptr;
     if (rec_out && n_out) {
-      if (host_io) TRY(tmp.alloc(&rec_d, n_out));
+      if (host_rec) TRY(tmp.alloc(&rec_d, n_out));
       else rec_d = rec_out;
     }
     Prop &P = st->P;
@@ -1110,7 +1116,7 @@ static int forward_save(wp_ctx *c, const wp_grid *grid, const float *m, const fl
       TRY(prop_inject(P, st->dsrc, st->wavelet, n, prv.p, nullptr, nullptr));
       if (rec_d) TRY(prop_sample(P, st->drec, prv.p, rec_d, n));
     }
-    if (host_io && rec_d) CU(cudaMemcpyAsync(rec_out, rec_d, n_out * 4, cudaMemcpyDeviceToHost, c->stream));
+    if (host_rec && rec_d) CU(cudaMemcpyAsync(rec_out, rec_d, n_out * 4, cudaMemcpyDeviceToHost, c->stream));
     TRY(ctx_wait(c, "forward with snapshots"));
     keep.release_all_to(st->mem);
     return WP_OK;
@@ -1124,7 +1130,9 @@ static int forward_save(wp_ctx *c, const wp_grid *grid, const float *m, const fl
   return WP_OK;
 }
 
-static int backward(wp_state *st, const float *residual, float *grad_out, bool host_io) {
+// host_res: the residual is a host array; host_grad: grad_out is a host array.
+static int backward(wp_state *st, const float *residual, float *grad_out, bool host_res, bool host_grad) {
+  const bool host_io = host_res;
   wp_ctx *c = st->c;
   const Geom &G = st->G;
   Prop &P = st->P;
@@ -1178,7 +1186,7 @@ static int backward(wp_state *st, const float *residual, float *grad_out, bool h
   }
   // pitched -> contiguous
   CU(cudaMemcpy2DAsync(grad_out, size_t(G.nx) * 4, g.p, size_t(G.pitch) * 4, size_t(G.nx) * 4,
-                       size_t(G.ny) * G.nz, host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
+                       size_t(G.ny) * G.nz, host_grad ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
   return ctx_wait(c, "backward (recompute, adjoint, gradient)");
 }
 
@@ -1233,8 +1241,9 @@ void wp_destroy(wp_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream && !c->broken) cudaStreamSynchronize(c->stream);
-  for (auto &kv : c->live) cudaFree(kv.first);
-  for (auto &kv : c->cache) cudaFree(kv.second);
+  for (auto &kv : c->live) cudaFreeAsync(kv.first, c->stream);
+  for (auto &kv : c->cache) cudaFreeAsync(kv.second, c->stream);
+  if (c->stream && !c->broken) cudaStreamSynchronize(c->stream);
   if (c->d_scalars) cudaFree(c->d_scalars);
   if (c->h_scalars) cudaFreeHost(c->h_scalars);
   for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
@@ -1336,8 +1345,8 @@ static int gradient_impl(wp_ctx *c, const wp_grid *grid, const float *m, const f
                          int nsrc, const double *src, const float *residual, int nrec, const double *rec, int S,
                          float *grad_out, bool host_io) {
   wp_state *st = nullptr;
-  TRY(forward_save(c, grid, m, eta, wavelet, nsrc, src, nrec, rec, S, nullptr, host_io, &st));
-  int rc = backward(st, residual, grad_out, host_io);
+  TRY(forward_save(c, grid, m, eta, wavelet, nsrc, src, nrec, rec, S, nullptr, host_io, host_io, &st));
+  int rc = backward(st, residual, grad_out, host_io, host_io);
   state_release(st);
   delete st;
   return rc;
@@ -1357,19 +1366,105 @@ int wp_gradient_dev(wp_ctx *c, const wp_grid *grid, const float *m, const float 
                gradient_impl(c, grid, m, eta, wavelet, nsrc, src, residual, nrec, rec, S, grad_out, false));
 }
 
+// FWI objective and gradient of one shot: forward with snapshots, r = d - d_obs
+// and J = 1/2 ||r||^2, backward with r.
+static int fwi_gradient_impl(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta,
+                             const float *wavelet, int nsrc, const double *src, const float *d_obs, int nrec,
+                             const double *rec, int S, float *grad_out, double *misfit, bool host_io) {
+  Geom G;
+  TRY(make_geom(grid, &G));
+  if (nrec < 0) return fail(WP_EINVAL, "point counts must be >= 0");
+  const size_t n = size_t(G.nt) * size_t(nrec);
+  if (n && !d_obs) return fail(WP_EINVAL, "d_obs is NULL");
+  if (host_io && n && !all_finite(d_obs, n)) return fail(WP_ENONFINITE, "d_obs holds NaN or Inf");
+  Arena tmp(c);
+  float *d = nullptr, *r = nullptr, *dobs_d = nullptr;
+  double *partial = nullptr;
+  const int max_blocks = 1024;
+  if (n) {
+    TRY(tmp.alloc(&d, n));
+    TRY(tmp.alloc(&r, n));
+    TRY(tmp.alloc(&partial, size_t(max_blocks)));
+    if (host_io) {
+      TRY(tmp.alloc(&dobs_d, n));
+      CU(cudaMemcpyAsync(dobs_d, d_obs, n * 4, cudaMemcpyHostToDevice, c->stream));
+    } else {
+      dobs_d = const_cast<float *>(d_obs);
+    }
+  }
+  wp_state *st = nullptr;
+  TRY(forward_save(c, grid, m, eta, wavelet, nsrc, src, nrec, rec, S, d, host_io, false, &st));
+  int rc = [&]() -> int {
+    double J = 0.0;
+    if (n) {
+      int used = 0;
+      CU(launch_residual(c->stream, d, dobs_d, r, (long long)n, partial, max_blocks, &used));
+      c->launches++;
+      std::vector<double> h(static_cast<size_t>(used));
+      CU(cudaMemcpyAsync(h.data(), partial, size_t(used) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      TRY(ctx_wait(c, "residual"));
+      for (double v : h) J += v;
+      J *= 0.5;
+    }
+    if (misfit) *misfit = J;
+    if (!std::isfinite(J)) return fail(WP_ENONFINITE, "d_obs or the modelled data holds NaN or Inf");
+    return backward(st, r, grad_out, false, host_io);
+  }();
+  state_release(st);
+  delete st;
+  return rc;
+}
+
 int wp_forward_save(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *wavelet, int nsrc,
                     const double *src, int nrec, const double *rec, int S, float *rec_out, void *stream,
                     wp_state **state) {
   if (!state) return fail(WP_EINVAL, "state is NULL");
   *state = nullptr;
   TRY(enter(c, stream));
-  return leave(c, stream, forward_save(c, grid, m, eta, wavelet, nsrc, src, nrec, rec, S, rec_out, false, state));
+  return leave(c, stream,
+               forward_save(c, grid, m, eta, wavelet, nsrc, src, nrec, rec, S, rec_out, false, false, state));
 }
 
 int wp_backward(wp_state *st, const float *residual, float *grad_out, void *stream) {
   if (!st) return fail(WP_EINVAL, "state is NULL");
   TRY(enter(st->c, stream));
-  return leave(st->c, stream, backward(st, residual, grad_out, false));
+  return leave(st->c, stream, backward(st, residual, grad_out, false, false));
+}
+
+int wp_fwi_gradient(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *wavelet, int nsrc,
+                    const double *src, const float *d_obs, int nrec, const double *rec, int S, float *grad_out,
+                    double *misfit) {
+  TRY(enter(c, nullptr));
+  return leave(c, nullptr,
+               fwi_gradient_impl(c, grid, m, eta, wavelet, nsrc, src, d_obs, nrec, rec, S, grad_out, misfit, true));
+}
+
+int wp_fwi_gradient_dev(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *wavelet,
+                        int nsrc, const double *src, const float *d_obs, int nrec, const double *rec, int S,
+                        float *grad_out, double *misfit, void *stream) {
+  TRY(enter(c, stream));
+  return leave(c, stream,
+               fwi_gradient_impl(c, grid, m, eta, wavelet, nsrc, src, d_obs, nrec, rec, S, grad_out, misfit, false));
+}
+
+int wp_set_budget(wp_ctx *c, size_t bytes) {
+  if (!c) return fail(WP_EINVAL, "context is NULL");
+  c->budget = bytes;
+  return WP_OK;
+}
+
+int wp_trim(wp_ctx *c, size_t keep_bytes) {
+  if (!c) return fail(WP_EINVAL, "context is NULL");
+  CU(cudaSetDevice(c->device));
+  CU(cudaStreamSynchronize(c->stream));
+  while (!c->cache.empty() && c->in_use > keep_bytes) {
+    auto it = std::prev(c->cache.end());
+    cudaFreeAsync(it->second, c->stream);
+    c->in_use -= it->first;
+    c->cache.erase(it);
+  }
+  CU(cudaStreamSynchronize(c->stream));  // lets the stream-ordered pool hand the memory back
+  return WP_OK;
 }
 
 void wp_state_free(wp_state *st) {

@@ -209,6 +209,38 @@ cudaError_t launch_interp(cudaStream_t st, const InterpArgs &a) {
   return cudaGetLastError();
 }
 
+// Residual of the misfit J = 1/2 ||d - d_obs||^2 (Eq. AS): r = d - d_obs, and one
+// double partial sum of r^2 per block, reduced in a fixed order (deterministic).
+__global__ void residual_kernel(const float *d, const float *d_obs, float *r, long long n, double *partial) {
+  __shared__ double warp_sum[8];
+  double acc = 0.0;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const float v = d[i] - d_obs[i];
+    r[i] = v;
+    acc += static_cast<double>(v) * v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += warp_sum[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+cudaError_t launch_residual(cudaStream_t st, const float *d, const float *d_obs, float *r, long long n,
+                            double *partial, int max_blocks, int *blocks_used) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > max_blocks) blocks = max_blocks;
+  if (blocks < 1) blocks = 1;
+  *blocks_used = static_cast<int>(blocks);
+  residual_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(d, d_obs, r, n, partial);
+  return cudaGetLastError();
+}
+
 __global__ void set_row_kernel(long long *p, long long v) { *p = v; }
 __global__ void add_row_kernel(long long *p, long long d) { *p += d; }
 

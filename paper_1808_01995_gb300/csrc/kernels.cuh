@@ -95,6 +95,11 @@ cudaError_t launch_set_row(cudaStream_t st, long long *p, long long v);
 cudaError_t launch_add_row(cudaStream_t st, long long *p, long long d);
 
 // ---- misc ----
+// r = d - d_obs over n samples; partial[b] = sum over block b's samples of r^2
+// (double), blocks of 256 threads; returns the number of blocks used (<= max_blocks)
+cudaError_t launch_residual(cudaStream_t st, const float *d, const float *d_obs, float *r, long long n,
+                            double *partial, int max_blocks, int *blocks_used);
+
 // bit 0 of *bad set if any of x[0..n) is NaN or Inf
 cudaError_t launch_check_finite(cudaStream_t st, const float *x, long long n, int *bad);
 

@@ -29,6 +29,7 @@ EXPORTED = [
     "wp_estimate_bytes", "wp_forward", "wp_adjoint", "wp_gradient", "wp_forward_dev", "wp_adjoint_dev",
     "wp_gradient_dev", "wp_propagate_dev", "wp_forward_save", "wp_backward", "wp_state_free",
     "wp_bytes_in_use", "wp_kernel_launches", "wp_set_profiling", "wp_profile_read",
+    "wp_fwi_gradient", "wp_fwi_gradient_dev", "wp_trim", "wp_set_budget",
 ]
 
 
@@ -118,6 +119,12 @@ def lib() -> ctypes.CDLL:
         "wp_set_profiling": ([_vp, _i], _i),
         "wp_profile_read": ([_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64), _i], _i),
         "wp_forward_noalloc": ([_gp, _fp, _fp, _fp, _i, _dp, _i, _dp, _fp, _vp], _i),
+        "wp_fwi_gradient": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _fp, _i, _dp, _i, _fp,
+                             ctypes.POINTER(ctypes.c_double)], _i),
+        "wp_fwi_gradient_dev": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _fp, _i, _dp, _i, _fp,
+                                 ctypes.POINTER(ctypes.c_double), _vp], _i),
+        "wp_trim": ([_vp, ctypes.c_size_t], _i),
+        "wp_set_budget": ([_vp, ctypes.c_size_t], _i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -331,6 +338,43 @@ def wp_forward_save(ctx: int, grid: Grid, m, eta, wavelet, src, rec, snap_interv
 
 def wp_backward(state: int, residual, grad_out, stream=None) -> None:
     _check(lib().wp_backward(state, _ptr(residual), _ptr(_dev_f32(grad_out, "grad_out")), _stream(stream)))
+
+
+def wp_fwi_gradient(ctx: int, grid: Grid, m, eta, wavelet, src, d_obs, rec, snap_interval: int):
+    """(gradient of J = 1/2 ||d - d_obs||^2 w.r.t. m, J) for host arrays."""
+    m = _host_f32(m, grid.shape)
+    eta = _host_f32(eta, grid.shape)
+    src = _coords(src, grid.ndim)
+    rec = _coords(rec, grid.ndim)
+    q = _host_f32(wavelet, (grid.nt, len(src)))
+    dobs = _host_f32(d_obs, (grid.nt, len(rec)))
+    out = np.zeros(grid.shape, dtype=np.float32)
+    J = ctypes.c_double()
+    g = grid.c()
+    _check(lib().wp_fwi_gradient(ctx, ctypes.byref(g), _ptr(m), _ptr(eta), _ptr(q), len(src), _ptr(src), _ptr(dobs),
+                                 len(rec), _ptr(rec), int(snap_interval), _ptr(out), ctypes.byref(J)))
+    return out, J.value
+
+
+def wp_fwi_gradient_dev(ctx: int, grid: Grid, m, eta, wavelet, src, d_obs, rec, snap_interval, grad_out,
+                        stream=None) -> float:
+    src = _coords(src, grid.ndim)
+    rec = _coords(rec, grid.ndim)
+    g = grid.c()
+    J = ctypes.c_double()
+    _check(lib().wp_fwi_gradient_dev(ctx, ctypes.byref(g), _ptr(_dev_f32(m, "m")), _ptr(_dev_f32(eta, "eta")),
+                                     _ptr(wavelet), len(src), _ptr(src), _ptr(d_obs), len(rec), _ptr(rec),
+                                     int(snap_interval), _ptr(_dev_f32(grad_out, "grad_out")), ctypes.byref(J),
+                                     _stream(stream)))
+    return J.value
+
+
+def wp_trim(ctx: int, keep_bytes: int = 0) -> None:
+    _check(lib().wp_trim(ctx, ctypes.c_size_t(keep_bytes)))
+
+
+def wp_set_budget(ctx: int, hbm_budget_bytes: int) -> None:
+    _check(lib().wp_set_budget(ctx, ctypes.c_size_t(hbm_budget_bytes)))
 
 
 def wp_state_free(state: int) -> None:

@@ -168,3 +168,29 @@ def test_blobs_full_size_gradient_by_finite_differences(ctx, blobs):
     print(f"blobs 280^3 nt=1500: directional derivative vs centred FD {errs}")
     assert np.isfinite(g).all()
     assert min(errs) < 1e-2
+
+
+def test_fwi_gradient_call_matches_oracle(ctx):
+    """wp_fwi_gradient (host and device arrays): misfit and gradient of one shot."""
+    true = synth.random_case((22, 27, 30), 4, nsrc=1, nrec=14, nbl=5, seed=19, vmin=1800, vmax=2600)
+    rng = np.random.default_rng(6)
+    m0 = (true.m * (1.0 + 0.03 * smooth_random(true.shape, rng))).astype(np.float32)
+    nt, S = 70, 9
+    dt = 0.85 * O.cfl_dt(true.spacing, 4, 1.0 / math.sqrt(float(m0.min())))
+    og = O.Grid(true.shape, true.spacing, true.origin, 4, dt, nt)
+    wg = W.Grid(true.shape, true.spacing, true.origin, 4, dt, nt)
+    q = true.wavelet(dt, nt)
+    e32 = true.eta32()
+    d_obs = O.forward(og, true.m32(), e32, q, true.src, true.rec).astype(np.float32)
+    d0 = O.forward(og, m0, e32, q, true.src, true.rec)
+    J_ref = 0.5 * float(((d0 - d_obs) ** 2).sum())
+    g_ref = O.gradient(og, m0, e32, q, true.src, (d0 - d_obs).astype(np.float32), true.rec)
+    g, J = W.wp_fwi_gradient(ctx.handle, wg, m0, e32, q, true.src, d_obs, true.rec, S)
+    assert abs(J - J_ref) <= 1e-4 * J_ref
+    assert rel_l2(g, g_ref) < 1e-3
+    gd = torch.empty(true.shape, device="cuda")
+    Jd = W.wp_fwi_gradient_dev(ctx.handle, wg, torch.from_numpy(m0).cuda(), torch.from_numpy(e32).cuda(),
+                               torch.from_numpy(q).cuda(), true.src, torch.from_numpy(d_obs).cuda(), true.rec, S, gd)
+    torch.cuda.synchronize()
+    assert Jd == J
+    assert np.array_equal(gd.cpu().numpy(), g)
