@@ -64,14 +64,17 @@ def parse():
 # ---------------------------------------------------------------------------
 # distributed plumbing (replicas only)
 # ---------------------------------------------------------------------------
-def dist_init():
+def dist_init(backend: str | None = None):
+    """(world, rank, local_rank) from the torchrun environment; initialises the
+    process group for N > 1 (NCCL on GPUs, gloo otherwise)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        backend = "nccl"
-        dist.init_process_group(backend=backend)
+        if not dist.is_initialized():
+            dist.init_process_group(backend=backend or ("nccl" if torch.cuda.is_available() else "gloo"))
     return world, rank, local
 
 
@@ -82,13 +85,21 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """Maximum of a scalar over all ranks (the slowest rank's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(world, points_per_rank, seconds_max):
+    """Replicas: every rank updates the same number of points; the job's rate is
+    all ranks' points over the slowest rank's time (Gpts/s)."""
+    return world * points_per_rank / seconds_max / 1e9
 
 
 # ---------------------------------------------------------------------------
@@ -361,7 +372,7 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     ms = max_over_ranks(ms, world)
     npts = int(np.prod(model.shape))
-    value = world * npts * nt * args.steps / (ms * 1e-3) / 1e9
+    value = whole_job_rate(world, npts * nt * args.steps, ms * 1e-3)
 
     alg_bytes, _, ndamp = algorithmic_bytes_per_launch(model)
     peak, peak_kind = measured_peaks()
@@ -402,7 +413,7 @@ def run_ours(args):
             e2e_step()
         torch.cuda.synchronize()
         el = max_over_ranks(time.perf_counter() - t0, world)
-        e2e = {"value": world * npts * nt * ke / el / 1e9, "unit": "Gpts/s",
+        e2e = {"value": whole_job_rate(world, npts * nt * ke, el), "unit": "Gpts/s",
                "h2d_bytes_per_step": int(mhn.nbytes + ehn.nbytes + qhn.nbytes),
                "d2h_bytes_per_step": int(out_h.nbytes), "steps": ke,
                "call": "wp_forward (host arrays, pinned)"}
