@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--serving-slots", type=int, default=4)
     p.add_argument("--serving-scale", type=float, default=1.0,
                    help="scale of the request sizes and nt (1.0 = 128..320 x 128..320 x 128..200 + 40, nt 500..2000)")
+    p.add_argument("--gradient", type=int, default=3,
+                   help="timed FWI gradients of the 200^3 + 40 blobs workload (0 skips the gradient leg)")
     p.add_argument("--profile-every", type=int, default=10,
                    help="bracket every N-th stencil launch with CUDA events in the timed region")
     return p.parse_args()
@@ -324,6 +326,44 @@ def serving_leg(args):
                                    if plain_sat["shots_per_hour"] else None)}}
 
 
+def gradient_leg(args):
+    """FWI objective + gradient of one shot on the 3D gradient workload: 200^3
+    interior + 40-point layer (280^3), layered model with Gaussian blobs, start
+    model smoothed by a 20-point Gaussian, SO8, 1500 steps, snapshots every 10,
+    200 x 200 receivers (wp_fwi_gradient_dev, inputs resident in HBM)."""
+    import torch
+    from paper_1808_01995_gb300 import synth
+    from paper_1808_01995_gb300 import wavprop as W
+    true, start = synth.blobs_3d()
+    k, nt, S = 8, 1500, 10
+    dt = 0.9 * W.wp_cfl_dt(W.Grid(true.shape, true.spacing, true.origin, k), max(true.vmax, start.vmax))
+    grid = W.Grid(true.shape, true.spacing, true.origin, k, dt, nt)
+    ctx = W.Context(0)
+    q = torch.from_numpy(true.wavelet(dt, nt)).cuda()
+    eta = torch.from_numpy(true.eta32()).cuda()
+    m_true = torch.from_numpy(true.m32()).cuda()
+    d_obs = torch.zeros((nt, len(true.rec)), device="cuda")
+    W.wp_forward_dev(ctx.handle, grid, m_true, eta, q, true.src, true.rec, d_obs)
+    m0 = torch.from_numpy(start.m32()).cuda()
+    g = torch.empty_like(m0)
+    J = W.wp_fwi_gradient_dev(ctx.handle, grid, m0, eta, q, true.src, d_obs, true.rec, S, g)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.gradient):
+        J = W.wp_fwi_gradient_dev(ctx.handle, grid, m0, eta, q, true.src, d_obs, true.rec, S, g)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.gradient
+    npts = int(np.prod(true.shape))
+    peak = W.wp_bytes_in_use(ctx.handle)
+    ctx.close()
+    return {"workload": f"blobs3d 200^3 + 40 ({true.shape[0]}^3) SO8, nt={nt}, snapshots every {S}, "
+                        f"{len(true.rec)} receivers", "ms_per_gradient": ms,
+            "gpts_per_s": npts * nt / (ms * 1e-3) / 1e9, "misfit": J, "device_bytes": int(peak),
+            "passes": "forward with snapshots + recompute + adjoint with fused correlation"}
+
+
 def run_ours(args):
     world, rank, local = dist_init()
     import torch
@@ -418,6 +458,10 @@ def run_ours(args):
                "d2h_bytes_per_step": int(out_h.nbytes), "steps": ke,
                "call": "wp_forward (host arrays, pinned)"}
 
+    gradient = None
+    if args.gradient > 0 and rank == 0:
+        gradient = gradient_leg(args)
+
     serving = None
     if args.serving > 0 and rank == 0:
         serving = serving_leg(args)
@@ -433,7 +477,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": describe(model, nt, dt),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clk.summary(), "serving": serving}
+                "clocks": clk.summary(), "gradient": gradient, "serving": serving}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

@@ -46,11 +46,17 @@ class AcousticForward(torch.autograd.Function):
     def forward(ctx, m, eta, wavelet, prop):
         grid = prop.grid
         d = torch.empty((grid.nt, len(prop.rec)), device=m.device, dtype=torch.float32)
-        st = W.wp_forward_save(prop.context.handle, grid, m.detach(), eta.detach(), wavelet.detach(),
-                               prop.src, prop.rec, prop.snap_interval, d)
-        ctx.state = _State(st)
         ctx.prop = prop
         ctx.save_for_backward(m, eta)
+        if ctx.needs_input_grad[0]:
+            # keep the snapshots resident only when dL/dm can be asked for
+            st = W.wp_forward_save(prop.context.handle, grid, m.detach(), eta.detach(), wavelet.detach(),
+                                   prop.src, prop.rec, prop.snap_interval, d)
+            ctx.state = _State(st)
+        else:
+            W.wp_forward_dev(prop.context.handle, grid, m.detach(), eta.detach(), wavelet.detach(), prop.src,
+                             prop.rec, d)
+            ctx.state = None
         return d
 
     @staticmethod

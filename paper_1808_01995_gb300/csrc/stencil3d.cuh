@@ -37,14 +37,27 @@ constexpr int kTileFlagTY = 16;             // y extent of a damping-flag tile
 
 enum StencilMode : int { kModeFwd = 0, kModeAdjGrad = 1 };
 
+// Tile parameters of the high orders (R > 4), chosen by measurement; the -D
+// overrides exist for tuning sweeps.
+#ifndef WP_NY_HI
+#define WP_NY_HI 2
+#endif
+#ifndef WP_P_HI
+#define WP_P_HI 2
+#endif
+#ifndef WP_MINB_HI
+#define WP_MINB_HI 2
+#endif
+
 template <int R, int MODE>
 struct Cfg3d {
-  static constexpr int NY = (R <= 4 && MODE == kModeFwd) ? 4 : 2;  // rows per consumer thread
-  static constexpr int TY = kConsumerWarps * NY;                     // tile height
-  static constexpr int RX = (R + 3) / 4 * 4;                         // x halo rounded to 16 bytes
+  static constexpr int NY = MODE == kModeFwd ? (R <= 4 ? 4 : WP_NY_HI) : 2;  // rows per consumer thread
+  static constexpr int TY = kConsumerWarps * NY;                               // tile height
+  static constexpr int RX = (R + 3) / 4 * 4;                                   // x halo rounded to 16 bytes
   static constexpr int PW = kTX + 2 * RX;
   static constexpr int PH = TY + 2 * R;
-  static constexpr int P = R <= 4 ? 3 : 2;                           // planes in flight ahead
+  static constexpr int P = R <= 4 ? 3 : WP_P_HI;                               // planes in flight ahead
+  static constexpr int MINB = (R <= 4 || MODE != kModeFwd) ? 2 : WP_MINB_HI;   // CTAs per SM to fit
   static constexpr int NSU = R + 1 + P;                              // u ring depth
   static constexpr int NST = P + 1;                                  // tile ring depth
   static constexpr int NSTREAM = MODE == kModeAdjGrad ? 5 : 3;       // um, b, s [, uj, g]
@@ -73,7 +86,7 @@ struct Stencil3dArgs {
 
 // tm: [0] u^n (halo'd plane box), [1] u^{n-1}, [2] b, [3] s, [4] u^j, [5] g (tile boxes)
 template <int R, int MODE>
-__global__ void __launch_bounds__(kThreads3d, 2)
+__global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
     stencil3d_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_um,
                      const __grid_constant__ CUtensorMap tm_b, const __grid_constant__ CUtensorMap tm_s,
                      const __grid_constant__ CUtensorMap tm_uj, const __grid_constant__ CUtensorMap tm_g,

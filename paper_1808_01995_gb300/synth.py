@@ -226,10 +226,12 @@ def blobs_3d(n: int = 200, h: float = 10.0, nbl: int = 40, nt: int = 1500, nrec_
 
 
 def salt_3d(nx: int = 512, ny: int = 512, nz: int = 400, h: float = 10.0, nbl: int = 40,
-            nt: int = 3000, nrec_side: int = 256, space_order: int = 16, seed: int | None = None):
+            nt: int = 3000, nrec_side: int = 256, space_order: int = 16, seed: int | None = None,
+            with_salt: bool = True):
     """Large 3D case: linear 1.5 -> 4 km/s background with a 4.5 km/s salt body
     between a seeded smooth top surface (6 low-wavenumber cosines) and a flat
-    base; 25 Hz source; nrec_side^2 receivers at 20 m depth."""
+    base; 25 Hz source; nrec_side^2 receivers at 20 m depth.  with_salt=False
+    gives the background alone (an FWI start model with the same geometry)."""
     rng = np.random.default_rng(BASE_SEED + 5 if seed is None else seed)
     z = np.arange(nz, dtype=np.float64)
     v = np.broadcast_to((1500.0 + 2500.0 * z / (nz - 1)).reshape(nz, 1, 1), (nz, ny, nx)).copy()
@@ -241,7 +243,8 @@ def salt_3d(nx: int = 512, ny: int = 512, nz: int = 400, h: float = 10.0, nbl: i
         top += rng.uniform(0.02, 0.06) * nz * np.cos(2 * math.pi * (ky * yy + kx * xx) + ph)
     base = int(0.75 * nz)
     inside = (z.reshape(nz, 1, 1) >= top[None]) & (z.reshape(nz, 1, 1) < base)
-    v[inside] = 4500.0
+    if with_salt:
+        v[inside] = 4500.0
     cy, cx = (ny - 1) * h / 2.0, (nx - 1) * h / 2.0
     src = [[20.0, cy, cx]]
     py = (ny - 1) * h / max(nrec_side - 1, 1)
