@@ -313,7 +313,7 @@ static int make_geom(const wp_grid *g, Geom *G, bool need_dt = true) {
   G->nfield = G->plane * G->nz;
   G->npoints = static_cast<long long>(G->nx) * G->ny * G->nz;
   if (G->nfield > (1ll << 36)) return fail(WP_EINVAL, "grid too large");
-  G->tiles_x = (G->nx + kTX - 1) / kTX;
+  G->tiles_x = (G->nx + kFlagTX - 1) / kFlagTX;  // damping-flag columns
   G->tiles_y = (G->ny + kTileFlagTY - 1) / kTileFlagTY;  // damping-flag rows
   G->nzw = (G->nz + 31) / 32;
   return WP_OK;
@@ -470,7 +470,7 @@ static int make_map(CUtensorMap *m, const float *base, const Geom &G, int bx, in
   return WP_OK;
 }
 
-static int halo_box_w(int R) { return kTX + 2 * ((R + 3) / 4 * 4); }
+static int halo_box_w(int R, int mode) { return stencil3d_tile_x(R, mode) + 2 * ((R + 3) / 4 * 4); }
 
 // A field and its TMA descriptors: the halo'd plane box of the forward and of the
 // adjoint+gradient stencil (their tiles differ in height).
@@ -483,9 +483,9 @@ struct Field3 {
 static int make_field_maps(Field3 *f, const Geom &G) {
   if (G.ndim != 3) return WP_OK;
   for (int mode = 0; mode < 2; ++mode) {
-    const int ty = stencil3d_tile_y(G.R, mode);
-    TRY(make_map(&f->halo[mode], f->p, G, halo_box_w(G.R), ty + 2 * G.R));
-    TRY(make_map(&f->tile[mode], f->p, G, kTX, ty));
+    const int tx = stencil3d_tile_x(G.R, mode), ty = stencil3d_tile_y(G.R, mode);
+    TRY(make_map(&f->halo[mode], f->p, G, halo_box_w(G.R, mode), ty + 2 * G.R));
+    TRY(make_map(&f->tile[mode], f->p, G, tx, ty));
   }
   f->mapped = true;
   return WP_OK;
@@ -501,8 +501,8 @@ struct Plan3d {
 
 static Plan3d plan3d(const Geom &G, int mode, int num_sms, int occ) {
   Plan3d p;
-  const int ty = stencil3d_tile_y(G.R, mode);
-  p.tiles_x = (G.nx + kTX - 1) / kTX;
+  const int tx = stencil3d_tile_x(G.R, mode), ty = stencil3d_tile_y(G.R, mode);
+  p.tiles_x = (G.nx + tx - 1) / tx;
   p.tiles_y = (G.ny + ty - 1) / ty;
   const long long tiles = static_cast<long long>(p.tiles_x) * p.tiles_y;
   const long long ctas = static_cast<long long>(num_sms) * std::max(occ, 1);
@@ -573,7 +573,7 @@ static int prop_setup(wp_ctx *c, Arena &ar, const Geom &G, const float *m, const
     a.nzw = G.nzw;
     a.tiles_x = G.tiles_x;
     a.tiles_y = G.tiles_y;
-    a.tile_w = kTX;
+    a.tile_w = kFlagTX;
     a.tile_h = kTileFlagTY;
   }
   a.max_inv_m_bits = reinterpret_cast<unsigned int *>(c->d_scalars + 2);
@@ -687,6 +687,7 @@ static int prop_step(Prop &P, const Field3 &u, const Field3 &um, float *out, int
     a.nzw = G.nzw;
     a.tiles_x = pl.tiles_x;
     a.tiles_y = pl.tiles_y;
+    a.flag_tiles_x = G.tiles_x;
     a.flag_tiles_y = G.tiles_y;
     a.zchunk = pl.zchunk;
     a.nzc = pl.nzc;
@@ -1644,7 +1645,7 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
   ca.nzw = G.nzw;
   ca.tiles_x = G.tiles_x;
   ca.tiles_y = G.tiles_y;
-  ca.tile_w = kTX;
+  ca.tile_w = kFlagTX;
   ca.tile_h = kTileFlagTY;
   ca.max_inv_m_bits = reinterpret_cast<unsigned int *>(scal + 2);
   ca.bad = scal + 1;
@@ -1670,13 +1671,13 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
   CUtensorMap halo[2], tile[2], tb, ts;
   Plan3d pl;
   if (G.ndim == 3) {
-    const int ty = stencil3d_tile_y(G.R, kModeFwd);
+    const int tx = stencil3d_tile_x(G.R, kModeFwd), ty = stencil3d_tile_y(G.R, kModeFwd);
     for (int i = 0; i < 2; ++i) {
-      TRY(make_map(&halo[i], u[i], G, halo_box_w(G.R), ty + 2 * G.R));
-      TRY(make_map(&tile[i], u[i], G, kTX, ty));
+      TRY(make_map(&halo[i], u[i], G, halo_box_w(G.R, kModeFwd), ty + 2 * G.R));
+      TRY(make_map(&tile[i], u[i], G, tx, ty));
     }
-    TRY(make_map(&tb, b, G, kTX, ty));
-    TRY(make_map(&ts, s, G, kTX, ty));
+    TRY(make_map(&tb, b, G, tx, ty));
+    TRY(make_map(&ts, s, G, tx, ty));
     int smem = 0, occ = 0, ty_k = 0, dev = 0, nsm = 0;
     CU(prepare_stencil3d_fwd(G.R, &smem, &occ, &ty_k));
     CU(cudaGetDevice(&dev));
@@ -1698,6 +1699,7 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
       a.nzw = G.nzw;
       a.tiles_x = pl.tiles_x;
       a.tiles_y = pl.tiles_y;
+      a.flag_tiles_x = G.tiles_x;
       a.flag_tiles_y = G.tiles_y;
       a.zchunk = pl.zchunk;
       a.nzc = pl.nzc;

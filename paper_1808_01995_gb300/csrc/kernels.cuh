@@ -19,9 +19,14 @@ cudaError_t launch_stencil3d_adj(int R, dim3 grid, cudaStream_t st, const CUtens
 // sets the dynamic shared-memory limit; reports the CTA footprint, occupancy and tile height
 cudaError_t prepare_stencil3d_fwd(int R, int *smem_bytes, int *blocks_per_sm, int *tile_y);
 cudaError_t prepare_stencil3d_adj(int R, int *smem_bytes, int *blocks_per_sm, int *tile_y);
-// tile height (y) of the work tiles of each mode
+// tile width (x) and height (y) of the work tiles of each mode
+int stencil3d_tile_x_fwd(int R);
+int stencil3d_tile_x_adj(int R);
 int stencil3d_tile_y_fwd(int R);
 int stencil3d_tile_y_adj(int R);
+inline int stencil3d_tile_x(int R, int mode) {
+  return mode == 1 ? stencil3d_tile_x_adj(R) : stencil3d_tile_x_fwd(R);
+}
 inline int stencil3d_tile_y(int R, int mode) {
   return mode == 1 ? stencil3d_tile_y_adj(R) : stencil3d_tile_y_fwd(R);
 }

@@ -10,18 +10,20 @@
 // Eq. Grad:  g -= dt^-2 u^j [s (w^{j+1} - w^{j+2}) + b Lap w^{j+1}]  (the
 // injected part is added by the injection kernel).
 //
-// GB300 design.  Persistent CTAs walk (32 x TY tile, z-chunk) work items in a
+// GB300 design.  Persistent CTAs walk (TX x TY tile, z-chunk) work items in a
 // static round-robin order and stream each chunk up z.  A producer warp issues
 // TMA (cp.async.bulk.tensor) loads, P planes ahead of the compute, into two
 // shared rings guarded by full/empty mbarriers:
-//   - the halo'd u^n plane, (32 + 2 RX) x (TY + 2R), ring depth R + 1 + P (TMA's
+//   - the halo'd u^n plane, (TX + 2 RX) x (TY + 2R), ring depth R + 1 + P (TMA's
 //     zero fill outside the tensor supplies the Dirichlet ghosts);
 //   - the pointwise tiles u^{n-1}, b, s (and u^j, g), ring depth P + 1; s only for
 //     planes whose tile holds damping (per-tile z bitmask, one word per 32 planes).
-// 8 consumer warps compute; each thread owns NY consecutive rows of one column:
-// it loads that column of the plane once for all y neighbours, reads x
-// neighbours from the plane and keeps z neighbours in a register queue, so the
-// shared-memory traffic per point stays well under the SM's bandwidth.
+// 8 consumer warps compute.  Each lane owns NX adjacent x points (NX = 2: packed
+// FP32x2 arithmetic, FFMA2/FADD2, and 8-byte shared loads) in NY consecutive
+// rows: it loads its column of the plane once for all y neighbours, reads x
+// neighbours from the plane and keeps z neighbours in a register queue.  This
+// keeps both the shared-memory traffic and the instructions issued per point
+// low enough for HBM to be the bound.
 // Every wait is bounded (%globaltimer); a timeout sets an abort flag, the
 // producer lets its copies land, and the error word reports it.
 #pragma once
@@ -30,42 +32,51 @@
 
 namespace wp {
 
-constexpr int kTX = 32;                     // tile width (x), one warp
 constexpr int kConsumerWarps = 8;
 constexpr int kThreads3d = (kConsumerWarps + 1) * 32;
+constexpr int kFlagTX = 32;                 // x extent of a damping-flag tile
 constexpr int kTileFlagTY = 16;             // y extent of a damping-flag tile
 
 enum StencilMode : int { kModeFwd = 0, kModeAdjGrad = 1 };
 
-// Tile parameters of the high orders (R > 4), chosen by measurement; the -D
-// overrides exist for tuning sweeps.
+// Tile parameters, chosen by measurement; the -D overrides exist for sweeps.
+#ifndef WP_NX
+#define WP_NX 2          // x points per lane
+#endif
+#ifndef WP_NY_LO
+#define WP_NY_LO 2       // rows per lane, R <= 4
+#endif
 #ifndef WP_NY_HI
-#define WP_NY_HI 2
+#define WP_NY_HI 2       // rows per lane, R > 4
 #endif
 #ifndef WP_P_HI
-#define WP_P_HI 2
+#define WP_P_HI 2        // planes in flight, R > 4
 #endif
 #ifndef WP_MINB_HI
-#define WP_MINB_HI 2
+#define WP_MINB_HI 1     // CTAs per SM the compiler must fit, R > 4
 #endif
 
 template <int R, int MODE>
 struct Cfg3d {
-  static constexpr int NY = MODE == kModeFwd ? (R <= 4 ? 4 : WP_NY_HI) : 2;  // rows per consumer thread
-  static constexpr int TY = kConsumerWarps * NY;                               // tile height
-  static constexpr int RX = (R + 3) / 4 * 4;                                   // x halo rounded to 16 bytes
-  static constexpr int PW = kTX + 2 * RX;
+  static constexpr int NX = WP_NX;
+  static constexpr int NY = MODE == kModeFwd ? (R <= 4 ? WP_NY_LO : WP_NY_HI) : 2;
+  static constexpr int TX = 32 * NX;                                 // tile width
+  static constexpr int TY = kConsumerWarps * NY;                     // tile height
+  static constexpr int RX = (R + 3) / 4 * 4;                         // x halo rounded to 16 bytes
+  static constexpr int RE = (R + 1) / 2 * 2;                         // x window half-width (even)
+  static constexpr int PW = TX + 2 * RX;
   static constexpr int PH = TY + 2 * R;
-  static constexpr int P = R <= 4 ? 3 : WP_P_HI;                               // planes in flight ahead
-  static constexpr int MINB = (R <= 4 || MODE != kModeFwd) ? 2 : WP_MINB_HI;   // CTAs per SM to fit
+  static constexpr int P = R <= 4 ? 3 : WP_P_HI;                     // planes in flight ahead
+  static constexpr int MINB = R <= 4 ? 2 : WP_MINB_HI;               // CTAs per SM to fit
   static constexpr int NSU = R + 1 + P;                              // u ring depth
   static constexpr int NST = P + 1;                                  // tile ring depth
   static constexpr int NSTREAM = MODE == kModeAdjGrad ? 5 : 3;       // um, b, s [, uj, g]
   static constexpr int USLOT = ((PW * PH * 4 + 127) / 128) * 128;    // bytes per u slot
-  static constexpr int TSLOT = kTX * TY * 4;                         // bytes per tile
+  static constexpr int TSLOT = TX * TY * 4;                          // bytes per tile
   static constexpr int T_OFF = NSU * USLOT;
   static constexpr int BAR_OFF = T_OFF + NST * NSTREAM * TSLOT;
   static constexpr int SMEM = BAR_OFF + 2 * (NSU + NST) * 8 + NST * 4 + 16;
+  static_assert(RX >= RE, "x halo must cover the x window");
 };
 
 struct Stencil3dArgs {
@@ -75,14 +86,33 @@ struct Stencil3dArgs {
   float *out;                   // u^{n+1} (may alias u^{n-1})
   float *grad;                  // adjoint+gradient: gradient (read-modify-write)
   float neg_inv_dt2;            // -1 / dt^2
-  const unsigned *tbits;        // [flag_tiles_y][tiles_x][nzw]: bit z set where the tile row has eta != 0
-  int nzw;                      // 32-bit words per tile (ceil(nz / 32))
-  int tiles_x, tiles_y;         // work tiles (32 x TY)
-  int flag_tiles_y;
+  const unsigned *tbits;        // [flag_tiles_y][flag_tiles_x][nzw]: bit z set where the flag tile has eta != 0
+  int nzw;                      // 32-bit words per flag tile (ceil(nz / 32))
+  int flag_tiles_x, flag_tiles_y;
+  int tiles_x, tiles_y;         // work tiles (TX x TY)
   int zchunk, nzc;              // planes per item, chunks per column
   int nitems;                   // tiles_x * tiles_y * nzc
   int *err;
 };
+
+// ---- scalar / packed-pair arithmetic -------------------------------------
+template <int NX> struct Vec;
+template <> struct Vec<1> { typedef float T; };
+template <> struct Vec<2> { typedef float2 T; };
+
+__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return a * b; }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b
+__device__ __forceinline__ float vsub(float a, float b) { return a - b; }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+template <class V> __device__ __forceinline__ V vsplat(float c);
+template <> __device__ __forceinline__ float vsplat<float>(float c) { return c; }
+template <> __device__ __forceinline__ float2 vsplat<float2>(float c) { return make_float2(c, c); }
+template <class V> __device__ __forceinline__ V vld(const float *p) { return *reinterpret_cast<const V *>(p); }
 
 // tm: [0] u^n (halo'd plane box), [1] u^{n-1}, [2] b, [3] s, [4] u^j, [5] g (tile boxes)
 template <int R, int MODE>
@@ -92,7 +122,8 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
                      const __grid_constant__ CUtensorMap tm_uj, const __grid_constant__ CUtensorMap tm_g,
                      const Stencil3dArgs a) {
   using C = Cfg3d<R, MODE>;
-  constexpr int NY = C::NY, TY = C::TY, TT = kTX * TY;
+  constexpr int NX = C::NX, NY = C::NY, TX = C::TX, TY = C::TY, TT = TX * TY;
+  using V = typename Vec<NX>::T;
   extern __shared__ __align__(128) unsigned char smem[];
   float *uring = reinterpret_cast<float *>(smem);
   float *tring = reinterpret_cast<float *>(smem + C::T_OFF);  // [NST][NSTREAM][TT]
@@ -185,22 +216,23 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
         int tx, ty, z0, z1;
         item_geom(item, tx, ty, z0, z1);
         if (z0 >= z1) continue;
-        const int x0 = tx * kTX, y0 = ty * TY;
-        // damping bits of the flag rows covered by this work tile
-        const int fy0 = y0 / kTileFlagTY;
-        const int fy1 = min(fy0 + TY / kTileFlagTY, a.flag_tiles_y);
+        const int x0 = tx * TX, y0 = ty * TY;
+        // damping bits of the flag tiles covered by this work tile
+        const int fx0 = x0 / kFlagTX, fx1 = min(fx0 + TX / kFlagTX, a.flag_tiles_x);
+        const int fy0 = y0 / kTileFlagTY, fy1 = min(fy0 + TY / kTileFlagTY, a.flag_tiles_y);
         auto word = [&](int w) -> unsigned {
           unsigned v = 0;
           if (w < a.nzw)
             for (int fy = fy0; fy < fy1; ++fy)
-              v |= __ldg(a.tbits + (static_cast<long long>(fy) * a.tiles_x + tx) * a.nzw + w);
+              for (int fx = fx0; fx < fx1; ++fx)
+                v |= __ldg(a.tbits + (static_cast<long long>(fy) * a.flag_tiles_x + fx) * a.nzw + w);
           return v;
         };
         int wcur = z0 >> 5;
         unsigned bits = word(wcur), bits_next = word(wcur + 1);
-        for (int p = z0; p < min(z0 + R, z1 + R) && ok; ++p) issue_u(x0, y0, p);
+        for (int p = z0; p < z0 + R && ok; ++p) issue_u(x0, y0, p);
         for (int z = z0; z < z1 && ok; ++z) {
-          if (z + R < z1 + R) issue_u(x0, y0, z + R);
+          issue_u(x0, y0, z + R);
           if ((z >> 5) != wcur) {
             wcur = z >> 5;
             bits = bits_next;
@@ -225,9 +257,10 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
   }
 
   // ---------------- consumers ----------------
-  const int ty0 = warp * NY;  // first tile row of this thread
-  uint32_t ub = 0;            // u-ring position of the current item's first plane
-  uint32_t tpos = 0;          // tile-ring position of the next plane
+  const int ty0 = warp * NY;          // first tile row of this lane
+  const int cx0 = C::RX + NX * lane;  // this lane's first column in a plane row
+  uint32_t ub = 0;                    // u-ring position of the current item's first plane
+  uint32_t tpos = 0;                  // tile-ring position of the next plane
   auto release = [&](uint64_t *bar) {
     __syncwarp();
     if (lane == 0) mbar_arrive(bar);
@@ -236,26 +269,35 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
     int tx, ty, z0, z1;
     item_geom(item, tx, ty, z0, z1);
     if (z0 >= z1) continue;
-    const int gx = tx * kTX + lane;
+    const int gx = tx * TX + NX * lane;
     const int y0 = ty * TY;
-    const bool xin = gx < a.g.nx;
+    const bool xin0 = gx < a.g.nx;
+    const bool xin1 = NX == 2 && gx + 1 < a.g.nx;
     bool yin[NY];
-    long long roff[NY];  // in-plane offset of each row (clamped inside the grid)
+    long long rbase[NY];  // in-plane offset of each row (row clamped inside the grid)
 #pragma unroll
     for (int r = 0; r < NY; ++r) {
       const int gy = y0 + ty0 + r;
-      yin[r] = xin && gy < a.g.ny;
-      roff[r] = static_cast<long long>(min(gy, a.g.ny - 1)) * a.g.pitch + min(gx, a.g.nx - 1);
+      yin[r] = gy < a.g.ny;
+      rbase[r] = static_cast<long long>(min(gy, a.g.ny - 1)) * a.g.pitch;
     }
+    const int gxc0 = min(gx, a.g.nx - 1), gxc1 = min(gx + 1, a.g.nx - 1);
 
     // z queue: q[r][j] = u^n at plane z - R + j
-    float q[NY][2 * R + 1];
+    V q[NY][2 * R + 1];
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       const int p = z0 - R + j;
 #pragma unroll
-      for (int r = 0; r < NY; ++r)
-        q[r][j] = (p >= 0 && yin[r]) ? __ldg(a.u + p * a.g.plane + roff[r]) : 0.f;
+      for (int r = 0; r < NY; ++r) {
+        const float *src = a.u + p * a.g.plane + rbase[r];
+        const bool ok = p >= 0 && yin[r];
+        if constexpr (NX == 2) {
+          q[r][j] = make_float2(ok && xin0 ? __ldg(src + gxc0) : 0.f, ok && xin1 ? __ldg(src + gxc1) : 0.f);
+        } else {
+          q[r][j] = ok && xin0 ? __ldg(src + gxc0) : 0.f;
+        }
+      }
     }
 #pragma unroll
     for (int j = 0; j < R; ++j) {
@@ -264,7 +306,7 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
       mbar_wait_bounded(&full_u[slot], (pos / C::NSU) & 1, abort_flag);
       const float *P = uring + slot * (C::USLOT / 4);
 #pragma unroll
-      for (int r = 0; r < NY; ++r) q[r][R + j] = P[(ty0 + r + R) * C::PW + lane + C::RX];
+      for (int r = 0; r < NY; ++r) q[r][R + j] = vld<V>(P + (ty0 + r + R) * C::PW + cx0);
       if (z0 + j >= z1) release(&empty_u[slot]);  // trailing plane of a short chunk: centre only
     }
 
@@ -276,26 +318,46 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
         mbar_wait_bounded(&full_u[slot], (pos / C::NSU) & 1, abort_flag);
         const float *P = uring + slot * (C::USLOT / 4);
 #pragma unroll
-        for (int r = 0; r < NY; ++r) q[r][2 * R] = P[(ty0 + r + R) * C::PW + lane + C::RX];
+        for (int r = 0; r < NY; ++r) q[r][2 * R] = vld<V>(P + (ty0 + r + R) * C::PW + cx0);
         if (z + R >= z1) release(&empty_u[slot]);
       }
       // x / y neighbours from the halo'd plane z (waited for as a centre plane)
       const uint32_t zslot = (ub + (z - z0)) % C::NSU;
       const float *P = uring + zslot * (C::USLOT / 4);
-      float lap[NY];
+      V lap[NY];
       {
-        float col[NY + 2 * R];
+        V col[NY + 2 * R];
 #pragma unroll
-        for (int i = 0; i < NY + 2 * R; ++i) col[i] = P[(ty0 + i) * C::PW + lane + C::RX];
+        for (int i = 0; i < NY + 2 * R; ++i) col[i] = vld<V>(P + (ty0 + i) * C::PW + cx0);
 #pragma unroll
         for (int r = 0; r < NY; ++r) {
-          const float *pc = P + (ty0 + r + R) * C::PW + lane + C::RX;
-          float l = a.c.c0 * q[r][R];
+          const float *pc = P + (ty0 + r + R) * C::PW + cx0;
+          V l = vmul(vsplat<V>(a.c.c0), q[r][R]);
+          if constexpr (NX == 2) {
+            // window w[k] = columns (cx0 - RE + 2k, +1): point 0 sits at RE, point 1 at RE + 1
+            float2 w[C::RE + 1];
 #pragma unroll
-          for (int j = 1; j <= R; ++j) {
-            l = fmaf(a.c.cx[j], pc[j] + pc[-j], l);
-            l = fmaf(a.c.cy[j], col[R + r + j] + col[R + r - j], l);
-            l = fmaf(a.c.cz[j], q[r][R + j] + q[r][R - j], l);
+            for (int k = 0; k <= C::RE; ++k) w[k] = vld<float2>(pc - C::RE + 2 * k);
+            auto win = [&](int i) -> float { return (i & 1) ? w[i >> 1].y : w[i >> 1].x; };
+#pragma unroll
+            for (int j = 1; j <= R; ++j) {
+              float2 xs;
+              if ((j & 1) == 0) {
+                xs = __fadd2_rn(w[(C::RE + j) >> 1], w[(C::RE - j) >> 1]);
+              } else {
+                xs = make_float2(win(C::RE + j) + win(C::RE - j), win(C::RE + 1 + j) + win(C::RE + 1 - j));
+              }
+              l = vfma(vsplat<V>(a.c.cx[j]), xs, l);
+              l = vfma(vsplat<V>(a.c.cy[j]), vadd(col[R + r + j], col[R + r - j]), l);
+              l = vfma(vsplat<V>(a.c.cz[j]), vadd(q[r][R + j], q[r][R - j]), l);
+            }
+          } else {
+#pragma unroll
+            for (int j = 1; j <= R; ++j) {
+              l = vfma(vsplat<V>(a.c.cx[j]), vadd(vld<V>(pc + j), vld<V>(pc - j)), l);
+              l = vfma(vsplat<V>(a.c.cy[j]), vadd(col[R + r + j], col[R + r - j]), l);
+              l = vfma(vsplat<V>(a.c.cz[j]), vadd(q[r][R + j], q[r][R - j]), l);
+            }
           }
           lap[r] = l;
         }
@@ -312,16 +374,33 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
       const bool live = !*abort_flag;
 #pragma unroll
       for (int r = 0; r < NY; ++r) {
-        const int ti = (ty0 + r) * kTX + lane;
-        const float c = q[r][R];
-        const float dd = c - T[ti];
-        const float sv = d ? T[2 * TT + ti] : 0.f;
-        const float bl = T[TT + ti] * lap[r];
-        const float un = fmaf(sv, dd, c + dd) + bl;
+        const int ti = (ty0 + r) * TX + NX * lane;
+        const V c = q[r][R];
+        const V dd = vsub(c, vld<V>(T + ti));
+        const V sv = d ? vld<V>(T + 2 * TT + ti) : vsplat<V>(0.f);
+        const V bl = vmul(vld<V>(T + TT + ti), lap[r]);
+        const V un = vadd(vfma(sv, dd, vadd(c, dd)), bl);
+        V gn = vsplat<V>(0.f);
+        if (MODE == kModeAdjGrad)
+          gn = vfma(vmul(vsplat<V>(a.neg_inv_dt2), vld<V>(T + 3 * TT + ti)), vfma(sv, dd, bl),
+                    vld<V>(T + 4 * TT + ti));
         if (yin[r] && live) {
-          a.out[po + roff[r]] = un;
-          if (MODE == kModeAdjGrad)
-            a.grad[po + roff[r]] = fmaf(a.neg_inv_dt2 * T[3 * TT + ti], fmaf(sv, dd, bl), T[4 * TT + ti]);
+          float *o = a.out + po + rbase[r] + gx;
+          float *gp = a.grad + po + rbase[r] + gx;
+          if constexpr (NX == 2) {
+            if (xin1) {
+              *reinterpret_cast<float2 *>(o) = un;
+              if (MODE == kModeAdjGrad) *reinterpret_cast<float2 *>(gp) = gn;
+            } else if (xin0) {
+              o[0] = un.x;
+              if (MODE == kModeAdjGrad) gp[0] = gn.x;
+            }
+          } else {
+            if (xin0) {
+              o[0] = un;
+              if (MODE == kModeAdjGrad) gp[0] = gn;
+            }
+          }
         }
       }
       release(&empty_t[tslot]);

@@ -39,6 +39,25 @@ cudaError_t launch_stencil3d_fwd(int R, dim3 grid, cudaStream_t st, const CUtens
 }
 
 template <int R>
+static int tile_x_t() {
+  return Cfg3d<R, kModeFwd>::TX;
+}
+
+int stencil3d_tile_x_fwd(int R) {
+  switch (R) {
+    case 1: return tile_x_t<1>();
+    case 2: return tile_x_t<2>();
+    case 3: return tile_x_t<3>();
+    case 4: return tile_x_t<4>();
+    case 5: return tile_x_t<5>();
+    case 6: return tile_x_t<6>();
+    case 7: return tile_x_t<7>();
+    case 8: return tile_x_t<8>();
+    default: return 32;
+  }
+}
+
+template <int R>
 static int tile_y_t() {
   return Cfg3d<R, kModeFwd>::TY;
 }
