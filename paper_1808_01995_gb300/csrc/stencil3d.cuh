@@ -28,6 +28,8 @@
 // producer lets its copies land, and the error word reports it.
 #pragma once
 
+#include <type_traits>
+
 #include "wp_device.cuh"
 
 namespace wp {
@@ -55,6 +57,13 @@ enum StencilMode : int { kModeFwd = 0, kModeAdjGrad = 1 };
 #ifndef WP_MINB_HI
 #define WP_MINB_HI 1     // CTAs per SM the compiler must fit, R > 4
 #endif
+#ifndef WP_MINB_LO
+#define WP_MINB_LO 2     // CTAs per SM the compiler must fit, R <= 4
+#endif
+#ifndef WP_ZU
+#define WP_ZU 2          // planes per unrolled z step (1..4)
+#endif
+
 
 template <int R, int MODE>
 struct Cfg3d {
@@ -67,7 +76,8 @@ struct Cfg3d {
   static constexpr int PW = TX + 2 * RX;
   static constexpr int PH = TY + 2 * R;
   static constexpr int P = R <= 4 ? 3 : WP_P_HI;                     // planes in flight ahead
-  static constexpr int MINB = R <= 4 ? 2 : WP_MINB_HI;               // CTAs per SM to fit
+  static constexpr int MINB = R <= 4 ? WP_MINB_LO : WP_MINB_HI;      // CTAs per SM to fit
+  static constexpr int ZU = WP_ZU;                                   // planes per unrolled z step
   static constexpr int NSU = R + 1 + P;                              // u ring depth
   static constexpr int NST = P + 1;                                  // tile ring depth
   static constexpr int NSTREAM = MODE == kModeAdjGrad ? 5 : 3;       // um, b, s [, uj, g]
@@ -150,6 +160,10 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
   }
   __syncthreads();
 
+  // Items of this CTA, round-robin: in every round the CTAs hold consecutive items
+  // (neighbouring tiles and a tile's adjacent z-chunks), so halos meet in L2.
+  const int item_end = a.nitems;
+  auto first_item = [&](int i) -> int { return blockIdx.x + i * gridDim.x; };
   auto item_geom = [&](int item, int &tx, int &ty, int &z0, int &z1) {
     const int tile = item / a.nzc, zc = item - tile * a.nzc;
     tx = tile % a.tiles_x;
@@ -212,14 +226,14 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
         }
         ++itt;
       };
-      for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x) {
+      for (int it = 0, item = first_item(0); item < item_end && ok; item = first_item(++it)) {
         int tx, ty, z0, z1;
         item_geom(item, tx, ty, z0, z1);
         if (z0 >= z1) continue;
         const int x0 = tx * TX, y0 = ty * TY;
         // damping bits of the flag tiles covered by this work tile
-        const int fx0 = x0 / kFlagTX, fx1 = min(fx0 + TX / kFlagTX, a.flag_tiles_x);
-        const int fy0 = y0 / kTileFlagTY, fy1 = min(fy0 + TY / kTileFlagTY, a.flag_tiles_y);
+        const int fx0 = x0 / kFlagTX, fx1 = min((x0 + TX - 1) / kFlagTX + 1, a.flag_tiles_x);
+        const int fy0 = y0 / kTileFlagTY, fy1 = min((y0 + TY - 1) / kTileFlagTY + 1, a.flag_tiles_y);
         auto word = [&](int w) -> unsigned {
           unsigned v = 0;
           if (w < a.nzw)
@@ -265,7 +279,7 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
     __syncwarp();
     if (lane == 0) mbar_arrive(bar);
   };
-  for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+  for (int it = 0, item = first_item(0); item < item_end; item = first_item(++it)) {
     int tx, ty, z0, z1;
     item_geom(item, tx, ty, z0, z1);
     if (z0 >= z1) continue;
@@ -283,8 +297,8 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
     }
     const int gxc0 = min(gx, a.g.nx - 1), gxc1 = min(gx + 1, a.g.nx - 1);
 
-    // z queue: q[r][j] = u^n at plane z - R + j
-    V q[NY][2 * R + 1];
+    // z queue: q[r][o + j] = u^n at plane z - R + j (o = offset of the plane in an unrolled step)
+    V q[NY][2 * R + C::ZU];
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       const int p = z0 - R + j;
@@ -310,104 +324,123 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
       if (z0 + j >= z1) release(&empty_u[slot]);  // trailing plane of a short chunk: centre only
     }
 
-    for (int z = z0; z < z1; ++z) {
-      // centre of plane z + R into the queue
-      {
-        const uint32_t pos = ub + (z + R - z0);
-        const uint32_t slot = pos % C::NSU;
-        mbar_wait_bounded(&full_u[slot], (pos / C::NSU) & 1, abort_flag);
-        const float *P = uring + slot * (C::USLOT / 4);
+    // One plane of the sweep; o (a compile-time offset) is where plane z - R sits
+    // in the queue, so an unrolled step of U planes rotates the queue only once.
+    auto plane = [&](int z, auto oc) {
+      constexpr int o = decltype(oc)::value;
+        // centre of plane z + R into the queue
+        {
+          const uint32_t pos = ub + (z + R - z0);
+          const uint32_t slot = pos % C::NSU;
+          mbar_wait_bounded(&full_u[slot], (pos / C::NSU) & 1, abort_flag);
+          const float *P = uring + slot * (C::USLOT / 4);
 #pragma unroll
-        for (int r = 0; r < NY; ++r) q[r][2 * R] = vld<V>(P + (ty0 + r + R) * C::PW + cx0);
-        if (z + R >= z1) release(&empty_u[slot]);
-      }
-      // x / y neighbours from the halo'd plane z (waited for as a centre plane)
-      const uint32_t zslot = (ub + (z - z0)) % C::NSU;
-      const float *P = uring + zslot * (C::USLOT / 4);
-      V lap[NY];
-      {
-        V col[NY + 2 * R];
+          for (int r = 0; r < NY; ++r) q[r][2 * R + o] = vld<V>(P + (ty0 + r + R) * C::PW + cx0);
+          if (z + R >= z1) release(&empty_u[slot]);
+        }
+        // x / y neighbours from the halo'd plane z (waited for as a centre plane)
+        const uint32_t zslot = (ub + (z - z0)) % C::NSU;
+        const float *P = uring + zslot * (C::USLOT / 4);
+        V lap[NY];
+        {
+          V col[NY + 2 * R];
 #pragma unroll
-        for (int i = 0; i < NY + 2 * R; ++i) col[i] = vld<V>(P + (ty0 + i) * C::PW + cx0);
+          for (int i = 0; i < NY + 2 * R; ++i) col[i] = vld<V>(P + (ty0 + i) * C::PW + cx0);
+#pragma unroll
+          for (int r = 0; r < NY; ++r) {
+            const float *pc = P + (ty0 + r + R) * C::PW + cx0;
+            V l = vmul(vsplat<V>(a.c.c0), q[r][o + R]);
+            if constexpr (NX == 2) {
+              // window w[k] = columns (cx0 - RE + 2k, +1): point 0 sits at RE, point 1 at RE + 1
+              float2 w[C::RE + 1];
+#pragma unroll
+              for (int k = 0; k <= C::RE; ++k) w[k] = vld<float2>(pc - C::RE + 2 * k);
+              auto win = [&](int i) -> float { return (i & 1) ? w[i >> 1].y : w[i >> 1].x; };
+#pragma unroll
+              for (int j = 1; j <= R; ++j) {
+                float2 xs;
+                if ((j & 1) == 0) {
+                  xs = __fadd2_rn(w[(C::RE + j) >> 1], w[(C::RE - j) >> 1]);
+                } else {
+                  xs = make_float2(win(C::RE + j) + win(C::RE - j), win(C::RE + 1 + j) + win(C::RE + 1 - j));
+                }
+                l = vfma(vsplat<V>(a.c.cx[j]), xs, l);
+                l = vfma(vsplat<V>(a.c.cy[j]), vadd(col[R + r + j], col[R + r - j]), l);
+                l = vfma(vsplat<V>(a.c.cz[j]), vadd(q[r][o + R + j], q[r][o + R - j]), l);
+              }
+            } else {
+#pragma unroll
+              for (int j = 1; j <= R; ++j) {
+                l = vfma(vsplat<V>(a.c.cx[j]), vadd(vld<V>(pc + j), vld<V>(pc - j)), l);
+                l = vfma(vsplat<V>(a.c.cy[j]), vadd(col[R + r + j], col[R + r - j]), l);
+                l = vfma(vsplat<V>(a.c.cz[j]), vadd(q[r][o + R + j], q[r][o + R - j]), l);
+              }
+            }
+            lap[r] = l;
+          }
+        }
+        release(&empty_u[zslot]);
+
+        // pointwise tiles of plane z
+        const uint32_t tslot = tpos % C::NST;
+        mbar_wait_bounded(&full_t[tslot], (tpos / C::NST) & 1, abort_flag);
+        ++tpos;
+        const float *T = tring + tslot * (C::NSTREAM * TT);
+        const bool d = sflag[tslot] != 0;
+        const long long po = static_cast<long long>(z) * a.g.plane;
+        const bool live = !*abort_flag;
 #pragma unroll
         for (int r = 0; r < NY; ++r) {
-          const float *pc = P + (ty0 + r + R) * C::PW + cx0;
-          V l = vmul(vsplat<V>(a.c.c0), q[r][R]);
-          if constexpr (NX == 2) {
-            // window w[k] = columns (cx0 - RE + 2k, +1): point 0 sits at RE, point 1 at RE + 1
-            float2 w[C::RE + 1];
-#pragma unroll
-            for (int k = 0; k <= C::RE; ++k) w[k] = vld<float2>(pc - C::RE + 2 * k);
-            auto win = [&](int i) -> float { return (i & 1) ? w[i >> 1].y : w[i >> 1].x; };
-#pragma unroll
-            for (int j = 1; j <= R; ++j) {
-              float2 xs;
-              if ((j & 1) == 0) {
-                xs = __fadd2_rn(w[(C::RE + j) >> 1], w[(C::RE - j) >> 1]);
-              } else {
-                xs = make_float2(win(C::RE + j) + win(C::RE - j), win(C::RE + 1 + j) + win(C::RE + 1 - j));
+          const int ti = (ty0 + r) * TX + NX * lane;
+          const V c = q[r][o + R];
+          const V dd = vsub(c, vld<V>(T + ti));
+          const V sv = d ? vld<V>(T + 2 * TT + ti) : vsplat<V>(0.f);
+          const V bl = vmul(vld<V>(T + TT + ti), lap[r]);
+          const V un = vadd(vfma(sv, dd, vadd(c, dd)), bl);
+          V gn = vsplat<V>(0.f);
+          if (MODE == kModeAdjGrad)
+            gn = vfma(vmul(vsplat<V>(a.neg_inv_dt2), vld<V>(T + 3 * TT + ti)), vfma(sv, dd, bl),
+                      vld<V>(T + 4 * TT + ti));
+          if (yin[r] && live) {
+            float *o = a.out + po + rbase[r] + gx;
+            float *gp = a.grad + po + rbase[r] + gx;
+            if constexpr (NX == 2) {
+              if (xin1) {
+                *reinterpret_cast<float2 *>(o) = un;
+                if (MODE == kModeAdjGrad) *reinterpret_cast<float2 *>(gp) = gn;
+              } else if (xin0) {
+                o[0] = un.x;
+                if (MODE == kModeAdjGrad) gp[0] = gn.x;
               }
-              l = vfma(vsplat<V>(a.c.cx[j]), xs, l);
-              l = vfma(vsplat<V>(a.c.cy[j]), vadd(col[R + r + j], col[R + r - j]), l);
-              l = vfma(vsplat<V>(a.c.cz[j]), vadd(q[r][R + j], q[r][R - j]), l);
-            }
-          } else {
-#pragma unroll
-            for (int j = 1; j <= R; ++j) {
-              l = vfma(vsplat<V>(a.c.cx[j]), vadd(vld<V>(pc + j), vld<V>(pc - j)), l);
-              l = vfma(vsplat<V>(a.c.cy[j]), vadd(col[R + r + j], col[R + r - j]), l);
-              l = vfma(vsplat<V>(a.c.cz[j]), vadd(q[r][R + j], q[r][R - j]), l);
+            } else {
+              if (xin0) {
+                o[0] = un;
+                if (MODE == kModeAdjGrad) gp[0] = gn;
+              }
             }
           }
-          lap[r] = l;
         }
-      }
-      release(&empty_u[zslot]);
+        release(&empty_t[tslot]);
 
-      // pointwise tiles of plane z
-      const uint32_t tslot = tpos % C::NST;
-      mbar_wait_bounded(&full_t[tslot], (tpos / C::NST) & 1, abort_flag);
-      ++tpos;
-      const float *T = tring + tslot * (C::NSTREAM * TT);
-      const bool d = sflag[tslot] != 0;
-      const long long po = static_cast<long long>(z) * a.g.plane;
-      const bool live = !*abort_flag;
-#pragma unroll
-      for (int r = 0; r < NY; ++r) {
-        const int ti = (ty0 + r) * TX + NX * lane;
-        const V c = q[r][R];
-        const V dd = vsub(c, vld<V>(T + ti));
-        const V sv = d ? vld<V>(T + 2 * TT + ti) : vsplat<V>(0.f);
-        const V bl = vmul(vld<V>(T + TT + ti), lap[r]);
-        const V un = vadd(vfma(sv, dd, vadd(c, dd)), bl);
-        V gn = vsplat<V>(0.f);
-        if (MODE == kModeAdjGrad)
-          gn = vfma(vmul(vsplat<V>(a.neg_inv_dt2), vld<V>(T + 3 * TT + ti)), vfma(sv, dd, bl),
-                    vld<V>(T + 4 * TT + ti));
-        if (yin[r] && live) {
-          float *o = a.out + po + rbase[r] + gx;
-          float *gp = a.grad + po + rbase[r] + gx;
-          if constexpr (NX == 2) {
-            if (xin1) {
-              *reinterpret_cast<float2 *>(o) = un;
-              if (MODE == kModeAdjGrad) *reinterpret_cast<float2 *>(gp) = gn;
-            } else if (xin0) {
-              o[0] = un.x;
-              if (MODE == kModeAdjGrad) gp[0] = gn.x;
-            }
-          } else {
-            if (xin0) {
-              o[0] = un;
-              if (MODE == kModeAdjGrad) gp[0] = gn;
-            }
-          }
-        }
-      }
-      release(&empty_t[tslot]);
+    };
+    auto rotate = [&](auto nc) {
+      constexpr int n = decltype(nc)::value;
 #pragma unroll
       for (int r = 0; r < NY; ++r)
 #pragma unroll
-        for (int j = 0; j < 2 * R; ++j) q[r][j] = q[r][j + 1];
+        for (int j = 0; j < 2 * R; ++j) q[r][j] = q[r][j + n];
+    };
+    int z = z0;
+    for (; z + C::ZU <= z1; z += C::ZU) {
+      plane(z, std::integral_constant<int, 0>{});
+      if constexpr (C::ZU > 1) plane(z + 1, std::integral_constant<int, 1>{});
+      if constexpr (C::ZU > 2) plane(z + 2, std::integral_constant<int, 2>{});
+      if constexpr (C::ZU > 3) plane(z + 3, std::integral_constant<int, 3>{});
+      rotate(std::integral_constant<int, C::ZU>{});
+    }
+    for (; z < z1; ++z) {
+      plane(z, std::integral_constant<int, 0>{});
+      rotate(std::integral_constant<int, 1>{});
     }
     ub += static_cast<uint32_t>(z1 + R - z0);
   }
