@@ -164,6 +164,15 @@ int wp_fwi_gradient_dev(wp_ctx *ctx, const wp_grid *grid, const float *m, const 
                         const float *d_obs, int nrec, const double *rec_coords, int snap_interval,
                         float *grad_out, double *misfit, void *stream);
 
+/* Multi-shot FWI (Sec. 3.4): the gradient of the objective summed over source
+ * experiments, and the fixed-step gradient update with bounds.
+ *   wp_axpy_dev:         y[i] += alpha x[i] for i < n (device arrays);
+ *   wp_update_model_dev: m[i] = min(max(m[i] - step grad[i], m_min), m_max),
+ *                        with 0 < m_min <= m_max (squared-slowness bounds). */
+int wp_axpy_dev(wp_ctx *ctx, long long n, float alpha, const float *x, float *y, void *stream);
+int wp_update_model_dev(wp_ctx *ctx, long long n, float step, const float *grad, float *m,
+                        float m_min, float m_max, void *stream);
+
 /* Release cached (not live) device blocks of the context until it holds at most
  * keep_bytes.  Waits for the context's stream first. */
 int wp_trim(wp_ctx *ctx, size_t keep_bytes);

@@ -1448,6 +1448,30 @@ int wp_fwi_gradient_dev(wp_ctx *c, const wp_grid *grid, const float *m, const fl
                fwi_gradient_impl(c, grid, m, eta, wavelet, nsrc, src, d_obs, nrec, rec, S, grad_out, misfit, false));
 }
 
+int wp_axpy_dev(wp_ctx *c, long long n, float alpha, const float *x, float *y, void *stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return fail(WP_EINVAL, "bad axpy arguments");
+  TRY(enter(c, stream));
+  int rc = [&]() -> int {
+    CU(launch_axpy(c->stream, n, alpha, x, y));
+    c->launches++;
+    return ctx_wait(c, "axpy");
+  }();
+  return leave(c, stream, rc);
+}
+
+int wp_update_model_dev(wp_ctx *c, long long n, float step, const float *grad, float *m, float m_min, float m_max,
+                        void *stream) {
+  if (n < 0 || (n > 0 && (!grad || !m)) || !(m_min > 0.f) || !(m_max >= m_min))
+    return fail(WP_EINVAL, "bad model-update arguments");
+  TRY(enter(c, stream));
+  int rc = [&]() -> int {
+    CU(launch_update_model(c->stream, n, step, grad, m, m_min, m_max));
+    c->launches++;
+    return ctx_wait(c, "model update");
+  }();
+  return leave(c, stream, rc);
+}
+
 int wp_set_budget(wp_ctx *c, size_t bytes) {
   if (!c) return fail(WP_EINVAL, "context is NULL");
   c->budget = bytes;

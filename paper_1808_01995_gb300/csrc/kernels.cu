@@ -241,6 +241,37 @@ cudaError_t launch_residual(cudaStream_t st, const float *d, const float *d_obs,
   return cudaGetLastError();
 }
 
+// Gradient sum over shots (Sec. 3.4): y += alpha x.
+__global__ void axpy_kernel(long long n, float alpha, const float *x, float *y) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    y[i] = fmaf(alpha, x[i], y[i]);
+}
+
+cudaError_t launch_axpy(cudaStream_t st, long long n, float alpha, const float *x, float *y) {
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  axpy_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(n, alpha, x, y);
+  return cudaGetLastError();
+}
+
+// Fixed-step gradient update with bounds (Sec. 3.4): m = clamp(m - step g, lo, hi).
+__global__ void update_model_kernel(long long n, float step, const float *g, float *m, float lo, float hi) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    m[i] = fminf(fmaxf(fmaf(-step, g[i], m[i]), lo), hi);
+}
+
+cudaError_t launch_update_model(cudaStream_t st, long long n, float step, const float *g, float *m, float lo,
+                                float hi) {
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  update_model_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(n, step, g, m, lo, hi);
+  return cudaGetLastError();
+}
+
 __global__ void set_row_kernel(long long *p, long long v) { *p = v; }
 __global__ void add_row_kernel(long long *p, long long d) { *p += d; }
 

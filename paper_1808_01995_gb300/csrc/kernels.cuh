@@ -105,6 +105,12 @@ cudaError_t launch_add_row(cudaStream_t st, long long *p, long long d);
 cudaError_t launch_residual(cudaStream_t st, const float *d, const float *d_obs, float *r, long long n,
                             double *partial, int max_blocks, int *blocks_used);
 
+// y[i] += alpha x[i], i < n
+cudaError_t launch_axpy(cudaStream_t st, long long n, float alpha, const float *x, float *y);
+// m[i] = min(max(m[i] - step g[i], lo), hi), i < n
+cudaError_t launch_update_model(cudaStream_t st, long long n, float step, const float *g, float *m, float lo,
+                                float hi);
+
 // bit 0 of *bad set if any of x[0..n) is NaN or Inf
 cudaError_t launch_check_finite(cudaStream_t st, const float *x, long long n, int *bad);
 

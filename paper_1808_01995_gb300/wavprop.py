@@ -29,7 +29,8 @@ EXPORTED = [
     "wp_estimate_bytes", "wp_forward", "wp_adjoint", "wp_gradient", "wp_forward_dev", "wp_adjoint_dev",
     "wp_gradient_dev", "wp_propagate_dev", "wp_forward_save", "wp_backward", "wp_state_free",
     "wp_bytes_in_use", "wp_kernel_launches", "wp_set_profiling", "wp_profile_read",
-    "wp_fwi_gradient", "wp_fwi_gradient_dev", "wp_trim", "wp_set_budget",
+    "wp_fwi_gradient", "wp_fwi_gradient_dev", "wp_trim", "wp_set_budget", "wp_axpy_dev",
+    "wp_update_model_dev",
 ]
 
 
@@ -125,6 +126,9 @@ def lib() -> ctypes.CDLL:
                                  ctypes.POINTER(ctypes.c_double), _vp], _i),
         "wp_trim": ([_vp, ctypes.c_size_t], _i),
         "wp_set_budget": ([_vp, ctypes.c_size_t], _i),
+        "wp_axpy_dev": ([_vp, ctypes.c_longlong, ctypes.c_float, _fp, _fp, _vp], _i),
+        "wp_update_model_dev": ([_vp, ctypes.c_longlong, ctypes.c_float, _fp, _fp, ctypes.c_float, ctypes.c_float,
+                                 _vp], _i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -371,6 +375,22 @@ def wp_fwi_gradient_dev(ctx: int, grid: Grid, m, eta, wavelet, src, d_obs, rec, 
 
 def wp_trim(ctx: int, keep_bytes: int = 0) -> None:
     _check(lib().wp_trim(ctx, ctypes.c_size_t(keep_bytes)))
+
+
+def wp_axpy_dev(ctx: int, alpha: float, x, y, stream=None) -> None:
+    """y += alpha x (contiguous float32 CUDA tensors of equal size)."""
+    if x.numel() != y.numel():
+        raise ValueError("x and y differ in size")
+    _check(lib().wp_axpy_dev(ctx, int(y.numel()), float(alpha), _ptr(_dev_f32(x, "x")), _ptr(_dev_f32(y, "y")),
+                             _stream(stream)))
+
+
+def wp_update_model_dev(ctx: int, step: float, grad, m, m_min: float, m_max: float, stream=None) -> None:
+    """m = clamp(m - step grad, m_min, m_max) in place."""
+    if grad.numel() != m.numel():
+        raise ValueError("grad and m differ in size")
+    _check(lib().wp_update_model_dev(ctx, int(m.numel()), float(step), _ptr(_dev_f32(grad, "grad")),
+                                     _ptr(_dev_f32(m, "m")), float(m_min), float(m_max), _stream(stream)))
 
 
 def wp_set_budget(ctx: int, hbm_budget_bytes: int) -> None:
