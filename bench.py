@@ -58,6 +58,10 @@ def parse():
                    help="scale of the request sizes and nt (1.0 = 128..320 x 128..320 x 128..200 + 40, nt 500..2000)")
     p.add_argument("--gradient", type=int, default=3,
                    help="timed FWI gradients of the 200^3 + 40 blobs workload (0 skips the gradient leg)")
+    p.add_argument("--checkpoints", type=int, default=20,
+                   help="stored states of the binomial-checkpointing gradient timed beside it (0 skips it)")
+    p.add_argument("--no-reconstruct", dest="reconstruct", action="store_false",
+                   help="skip the boundary-reconstruction gradient timed beside the snapshot one")
     p.add_argument("--profile-every", type=int, default=10,
                    help="bracket every N-th stencil launch with CUDA events in the timed region")
     return p.parse_args()
@@ -357,11 +361,47 @@ def gradient_leg(args):
     ms = e0.elapsed_time(e1) / args.gradient
     npts = int(np.prod(true.shape))
     peak = W.wp_bytes_in_use(ctx.handle)
+    # the same gradient with binomial checkpointing (given residual, own context for its memory)
+    d0 = torch.zeros_like(d_obs)
+    W.wp_forward_dev(ctx.handle, grid, m0, eta, q, true.src, true.rec, d0)
+    r = (d0 - d_obs).contiguous()
     ctx.close()
+    ck = {}
+    if args.checkpoints > 0:
+        cctx = W.Context(0)
+        gc = torch.empty_like(m0)
+        W.wp_gradient_checkpointed_dev(cctx.handle, grid, m0, eta, q, true.src, r, true.rec, args.checkpoints, gc)
+        torch.cuda.synchronize()
+        e0.record()
+        W.wp_gradient_checkpointed_dev(cctx.handle, grid, m0, eta, q, true.src, r, true.rec, args.checkpoints, gc)
+        e1.record()
+        torch.cuda.synchronize()
+        _, fw = W.wp_checkpoint_schedule(nt, args.checkpoints)
+        ck = {"checkpoints": args.checkpoints, "ms_per_gradient": e0.elapsed_time(e1),
+              "device_bytes": int(W.wp_bytes_in_use(cctx.handle)), "forward_steps": fw,
+              "same_as_snapshots": bool(torch.equal(gc, g))}
+        cctx.close()
+    rc = {}
+    if args.reconstruct:
+        rctx = W.Context(0)
+        gr = torch.empty_like(m0)
+        W.wp_gradient_reconstruct_dev(rctx.handle, grid, m0, eta, q, true.src, r, true.rec, gr)
+        torch.cuda.synchronize()
+        e0.record()
+        W.wp_gradient_reconstruct_dev(rctx.handle, grid, m0, eta, q, true.src, r, true.rec, gr)
+        e1.record()
+        torch.cuda.synchronize()
+        nb = true.nbl
+        inner = (slice(nb, -nb),) * 3
+        a, b = gr[inner].double(), g[inner].double()
+        rc = {"ms_per_gradient": e0.elapsed_time(e1), "device_bytes": int(W.wp_bytes_in_use(rctx.handle)),
+              "rel_l2_vs_snapshots_interior": float((a - b).norm() / b.norm())}
+        rctx.close()
     return {"workload": f"blobs3d 200^3 + 40 ({true.shape[0]}^3) SO8, nt={nt}, snapshots every {S}, "
                         f"{len(true.rec)} receivers", "ms_per_gradient": ms,
             "gpts_per_s": npts * nt / (ms * 1e-3) / 1e9, "misfit": J, "device_bytes": int(peak),
-            "passes": "forward with snapshots + recompute + adjoint with fused correlation"}
+            "passes": "forward with snapshots + recompute + adjoint with fused correlation",
+            "binomial_checkpointing": ck, "boundary_reconstruction": rc}
 
 
 def run_ours(args):

@@ -99,7 +99,9 @@ int wp_fd_weights(int space_order, double *alpha);
 int wp_cfl_dt(const wp_grid *grid, double vmax, double *dt_max);
 
 /* Device bytes a call would hold for this grid: mode 0 forward/adjoint,
- * 1 gradient with the given snapshot interval. */
+ * 1 gradient with the given snapshot interval, 2 checkpointed gradient with
+ * snap_interval stored states, 3 gradient by boundary reconstruction (an upper
+ * bound; snap_interval unused). */
 int wp_estimate_bytes(const wp_grid *grid, int nsrc, int nrec, int mode, int snap_interval,
                       size_t *bytes);
 
@@ -130,6 +132,40 @@ int wp_gradient(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *e
                 const float *residual, int nrec, const double *rec_coords, int snap_interval,
                 float *grad_out);
 
+/* Gradient as wp_gradient, with binomial checkpointing instead of periodic
+ * snapshots (Sec. 3.3: partial time history plus recomputation, as Revolve):
+ * `checkpoints` stored states (2 fields each) and the optimal reversal schedule
+ * for that number minimise the recomputed forward steps.  Memory: about
+ * 2 checkpoints + 7 fields instead of 2 nt/snap_interval + snap_interval + 5.
+ * The result is identical to wp_gradient's. */
+int wp_gradient_checkpointed(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *eta,
+                             const float *wavelet, int nsrc, const double *src_coords,
+                             const float *residual, int nrec, const double *rec_coords,
+                             int checkpoints, float *grad_out);
+
+/* Gradient by boundary-wavefield reconstruction (Sec. 3.3): the forward pass
+ * keeps only the values on a ring of width space_order/2 around the box Z where
+ * eta = 0 (for every time level), and the backward pass rebuilds u^j on Z by
+ * running the time-symmetric undamped update backward, beside the adjoint.
+ * Memory: O(surface x nt) instead of snapshots; cost: the same passes as
+ * wp_gradient.  grad_out receives the gradient on Z and 0 in the damping layer
+ * (where the forward field is not reversible); on Z it equals wp_gradient's up
+ * to FP32 rounding of the reversal.  WP_EINVAL if eta vanishes nowhere or the
+ * set where it vanishes is not an axis-aligned box. */
+int wp_gradient_reconstruct(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *eta,
+                            const float *wavelet, int nsrc, const double *src_coords,
+                            const float *residual, int nrec, const double *rec_coords,
+                            float *grad_out);
+
+/* The reversal schedule used by wp_gradient_checkpointed: 4 ints per op
+ * (kind, a, b, slot) with kind 0 = advance from the state a held in `slot` to
+ * state b, 1 = store the current state a in `slot`, 2 = adjoint step j = a;
+ * state k is (u^{k-1}, u^k) and slot 0 holds state 0.  *nops receives the
+ * number of ops (ops may be NULL to query it), *forward_steps the number of
+ * forward steps the schedule recomputes. */
+int wp_checkpoint_schedule(int nt, int checkpoints, int *ops, int max_ops, int *nops,
+                           long long *forward_steps);
+
 /* ---- DEVICE-array variants ------------------------------------------------
  * Same contracts; m, eta, wavelet, rec/src data and outputs are device pointers
  * (contiguous, float), coordinates stay on the host.  Work is ordered after
@@ -145,6 +181,15 @@ int wp_gradient_dev(wp_ctx *ctx, const wp_grid *grid, const float *m, const floa
                     const float *wavelet, int nsrc, const double *src_coords,
                     const float *residual, int nrec, const double *rec_coords,
                     int snap_interval, float *grad_out, void *stream);
+int wp_gradient_reconstruct_dev(wp_ctx *ctx, const wp_grid *grid, const float *m,
+                                const float *eta, const float *wavelet, int nsrc,
+                                const double *src_coords, const float *residual, int nrec,
+                                const double *rec_coords, float *grad_out, void *stream);
+int wp_gradient_checkpointed_dev(wp_ctx *ctx, const wp_grid *grid, const float *m,
+                                 const float *eta, const float *wavelet, int nsrc,
+                                 const double *src_coords, const float *residual, int nrec,
+                                 const double *rec_coords, int checkpoints, float *grad_out,
+                                 void *stream);
 
 /* nsteps source-free updates of (u_prev, u) = (u^{n-1}, u^n) in place (device
  * fields, contiguous): on return they hold (u^{n+nsteps-1}, u^{n+nsteps}). */

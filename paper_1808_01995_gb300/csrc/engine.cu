@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <string>
@@ -64,7 +65,7 @@ struct wp_ctx {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_done = nullptr;
   double timeout_s = 600.0;
-  int *d_scalars = nullptr;                // [0] error word, [1] bad-input bits, [2] max(1/m) bits
+  int *d_scalars = nullptr;                // [0] error word, [1] bad-input bits, [2] max(1/m) bits, [8..14] box
   int *h_scalars = nullptr;                // pinned mirror
   uint64_t launches = 0;
   int smem3d[2][9] = {};
@@ -1192,6 +1193,90 @@ static int backward(wp_state *st, const float *residual, float *grad_out, bool h
 }
 
 // ---------------------------------------------------------------------------
+// Binomial checkpointing (optimal reversal with a fixed number of stored states)
+// ---------------------------------------------------------------------------
+// State k is the pair (u^{k-1}, u^k); the adjoint step j needs state j.  With the
+// start state a stored and c free slots, n adjoint steps (j = a+n .. a+1) are
+// reversed either directly (n = 1: advance one step; c = 0: for each j advance
+// from a) or by advancing m steps, storing state a+m, reversing the upper n-m
+// steps with c-1 slots and then the lower m steps from a again.  The cost (forward
+// steps, one more for each store) obeys
+//     T(n, c) = min_m  m + 1 + T(n-m, c-1) + T(m, c),   T(1, c) = 1,   T(n, 0) = n(n+1)/2,
+// which is minimised by dynamic programming; the smallest optimal m is
+// nondecreasing in n, so each row is found by a forward scan.
+enum CkKind : int { kCkAdvance = 0, kCkStore = 1, kCkAdjoint = 2 };
+struct CkOp {
+  int kind, a, b, slot;  // advance: slot holding state a -> state b; store: state a -> slot; adjoint: j = a
+};
+
+struct CkTable {
+  int nt = 0, c = 0;
+  std::vector<long long> T;  // (nt+1) x (c+1)
+  std::vector<int> opt;
+  long long &t(int n, int k) { return T[size_t(n) * (c + 1) + k]; }
+  int &o(int n, int k) { return opt[size_t(n) * (c + 1) + k]; }
+};
+
+static void ck_build(CkTable &tb, int nt, int c) {
+  tb.nt = nt;
+  tb.c = c;
+  tb.T.assign(size_t(nt + 1) * (c + 1), 0);
+  tb.opt.assign(size_t(nt + 1) * (c + 1), 0);
+  for (int n = 0; n <= nt; ++n) tb.t(n, 0) = static_cast<long long>(n) * (n + 1) / 2;
+  for (int k = 1; k <= c; ++k) {
+    if (nt >= 1) tb.t(1, k) = 1;
+    int lo = 1;
+    for (int n = 2; n <= nt; ++n) {
+      long long best = tb.t(n, k - 1);  // using fewer slots is always possible
+      int bm = 0;
+      int rises = 0;
+      for (int m = lo; m < n; ++m) {
+        const long long v = m + 1 + tb.t(n - m, k - 1) + tb.t(m, k);
+        if (v < best || (bm == 0 && v == best)) {
+          best = v;
+          bm = m;
+          rises = 0;
+        } else if (bm && ++rises > 16) {
+          break;
+        }
+      }
+      tb.t(n, k) = best;
+      tb.o(n, k) = bm;  // 0: do not split at this level
+      if (bm) lo = bm;
+    }
+  }
+}
+
+// Op list reversing all nt steps from state 0 (slot 0) with `c` free slots 1..c.
+static void ck_schedule(CkTable &tb, std::vector<CkOp> &ops) {
+  std::vector<int> free_slots;
+  for (int k = tb.c; k >= 1; --k) free_slots.push_back(k);
+  // explicit recursion on the upper part (depth <= c); the lower part loops
+  std::function<void(int, int, int)> rev = [&](int a, int n, int slot) {
+    while (n > 0) {
+      // best split with at most the free slots (0: none pays off)
+      int m = 0;
+      for (int k = std::min(static_cast<int>(free_slots.size()), tb.c); n >= 2 && k >= 1 && !m; --k) m = tb.o(n, k);
+      if (n == 1 || m == 0) {
+        for (int i = n; i >= 1; --i) {
+          ops.push_back({kCkAdvance, a, a + i, slot});
+          ops.push_back({kCkAdjoint, a + i, 0, 0});
+        }
+        return;
+      }
+      const int t = free_slots.back();
+      free_slots.pop_back();
+      ops.push_back({kCkAdvance, a, a + m, slot});
+      ops.push_back({kCkStore, a + m, 0, t});
+      rev(a + m, n - m, t);
+      free_slots.push_back(t);
+      n = m;
+    }
+  };
+  rev(0, tb.nt, 0);
+}
+
+// ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
 extern "C" {
@@ -1313,6 +1398,14 @@ int wp_estimate_bytes(const wp_grid *grid, int nsrc, int nrec, int mode, int sna
     const int S = std::max(snap_interval, 1);
     const size_t nseg = (size_t(G.nt) + S - 1) / S;
     b += 2 * nseg * f + size_t(std::min(S, std::max(G.nt, 1)) + 2 + 3) * f;
+  } else if (mode == 2) {
+    b += (2 * size_t(std::max(snap_interval, 0)) + 2 + 3) * f;  // stored states + state 0 + adjoint + gradient
+  } else if (mode == 3) {
+    // two forward, two adjoint fields, the gradient, and the stored rings: a ring of
+    // width R around any box inside the grid has at most 2R x (the grid's surface) points
+    const size_t surf = G.ndim == 3 ? size_t(G.nx) * G.ny + size_t(G.ny) * G.nz + size_t(G.nz) * G.nx
+                                    : size_t(G.nx) + size_t(G.nz);
+    b += 5 * f + size_t(std::max(G.nt - 2, 0)) * 2 * G.R * surf * 4;
   }
   *bytes = b;
   return WP_OK;
@@ -1416,6 +1509,250 @@ static int fwi_gradient_impl(wp_ctx *c, const wp_grid *grid, const float *m, con
   return rc;
 }
 
+// Inputs of a one-shot gradient staged on the device: coefficients, point tables,
+// wavelet and residual (validated), two work fields W (which hold m and eta
+// while the coefficients are built from host arrays).
+struct GradSetup {
+  explicit GradSetup(wp_ctx *c) : ar(c) {}
+  Geom G;
+  Arena ar;
+  Field3 W[2];
+  Prop P;
+  DevPoints dsrc, drec;
+  const float *q_d = nullptr, *r_d = nullptr, *eta_d = nullptr;
+};
+
+static int grad_setup(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *wavelet,
+                      int nsrc, const double *src, const float *residual, int nrec, const double *rec,
+                      const float *grad_out, bool host_io, GradSetup &S) {
+  Geom &G = S.G;
+  TRY(make_geom(grid, &G));
+  if (nsrc < 0 || nrec < 0) return fail(WP_EINVAL, "point counts must be >= 0");
+  if (!m || !eta || !grad_out) return fail(WP_EINVAL, "m, eta and grad_out must not be NULL");
+  const size_t n_in = size_t(G.nt) * nsrc, n_res = size_t(G.nt) * nrec;
+  if (n_in && !wavelet) return fail(WP_EINVAL, "wavelet is NULL");
+  if (n_res && !residual) return fail(WP_EINVAL, "residual is NULL");
+  if (host_io && n_in && !all_finite(wavelet, n_in)) return fail(WP_ENONFINITE, "wavelet holds NaN or Inf");
+  if (host_io && n_res && !all_finite(residual, n_res)) return fail(WP_ENONFINITE, "residual holds NaN or Inf");
+  PointSet psrc, prec;
+  TRY(build_points(G, nsrc, src, &psrc, "source"));
+  TRY(build_points(G, nrec, rec, &prec, "receiver"));
+  TRY(alloc_field(S.ar, G, &S.W[0], false, c->stream));
+  TRY(alloc_field(S.ar, G, &S.W[1], false, c->stream));
+  const float *md = m, *ed = eta;
+  if (host_io) {
+    CU(cudaMemcpyAsync(S.W[0].p, m, G.npoints * 4, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(S.W[1].p, eta, G.npoints * 4, cudaMemcpyHostToDevice, c->stream));
+    md = S.W[0].p;
+    ed = S.W[1].p;
+  }
+  S.eta_d = ed;
+  TRY(prop_setup(c, S.ar, G, md, ed, &S.P));
+  TRY(upload_points(c, S.ar, psrc, false, true, &S.dsrc));
+  TRY(upload_points(c, S.ar, prec, false, true, &S.drec));
+  S.q_d = wavelet;
+  S.r_d = residual;
+  if (host_io && (n_in || n_res)) {
+    float *tmp = nullptr;
+    TRY(S.ar.alloc(&tmp, n_in + n_res));
+    if (n_in) CU(cudaMemcpyAsync(tmp, wavelet, n_in * 4, cudaMemcpyHostToDevice, c->stream));
+    if (n_res) CU(cudaMemcpyAsync(tmp + n_in, residual, n_res * 4, cudaMemcpyHostToDevice, c->stream));
+    S.q_d = tmp;
+    S.r_d = tmp + n_in;
+  } else if (!host_io && (n_in || n_res)) {
+    int *bad = c->d_scalars + 1;
+    CU(cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+    if (n_in) CU(launch_check_finite(c->stream, wavelet, (long long)n_in, bad));
+    if (n_res) CU(launch_check_finite(c->stream, residual, (long long)n_res, bad));
+    c->launches += (n_in ? 1 : 0) + (n_res ? 1 : 0);
+    CU(cudaMemcpyAsync(c->h_scalars + 1, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    TRY(ctx_wait(c, "input checks"));
+    if (c->h_scalars[1]) return fail(WP_ENONFINITE, "wavelet or residual holds NaN or Inf");
+  }
+  return WP_OK;
+}
+
+// pitched gradient -> the caller's contiguous array
+static int grad_copy_out(wp_ctx *c, const Geom &G, const Field3 &g, float *grad_out, bool host_io) {
+  CU(cudaMemcpy2DAsync(grad_out, size_t(G.nx) * 4, g.p, size_t(G.pitch) * 4, size_t(G.nx) * 4,
+                       size_t(G.ny) * G.nz, host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
+  return WP_OK;
+}
+
+// Gradient (as wp_gradient) with binomial checkpointing: `nslots` stored states
+// replace the periodic snapshots; the forward field is recomputed from state 0
+// and the stored states by the schedule of ck_schedule.
+static int gradient_ckpt_impl(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta,
+                              const float *wavelet, int nsrc, const double *src, const float *residual, int nrec,
+                              const double *rec, int nslots, float *grad_out, bool host_io) {
+  if (nslots < 0 || nslots > 4096) return fail(WP_EINVAL, "checkpoints must be in [0, 4096]");
+  GradSetup S(c);
+  TRY(grad_setup(c, grid, m, eta, wavelet, nsrc, src, residual, nrec, rec, grad_out, host_io, S));
+  const Geom &G = S.G;
+  Arena &ar = S.ar;
+  Field3 *W = S.W;
+  // state 0 = (0, 0) in slot 0; slots 1..nslots for stored states
+  std::vector<Field3> sp(size_t(nslots) + 1), sc(size_t(nslots) + 1);
+  for (int k = 0; k <= nslots; ++k) {
+    TRY(alloc_field(ar, G, &sp[size_t(k)], k == 0, c->stream));
+    TRY(alloc_field(ar, G, &sc[size_t(k)], k == 0, c->stream));
+  }
+  Field3 A[2], g;
+  TRY(alloc_field(ar, G, &A[0], true, c->stream));
+  TRY(alloc_field(ar, G, &A[1], true, c->stream));
+  TRY(alloc_field(ar, G, &g, true, c->stream));
+  CkTable tb;
+  ck_build(tb, G.nt, nslots);
+  std::vector<CkOp> ops;
+  ck_schedule(tb, ops);
+  const Field3 *cp = nullptr, *cc = nullptr;  // current state (u^{k-1}, u^k)
+  int state = -1;
+  long long kadj = 0;
+  auto is_work = [&](const Field3 *f) { return f == &W[0] || f == &W[1]; };
+  for (const CkOp &op : ops) {
+    if (op.kind == kCkAdvance) {
+      cp = &sp[size_t(op.slot)];
+      cc = &sc[size_t(op.slot)];
+      for (int k = op.a; k < op.b; ++k) {
+        Field3 *out = is_work(cp) ? const_cast<Field3 *>(cp) : (cc == &W[0] ? &W[1] : &W[0]);
+        TRY(prop_step(S.P, *cc, *cp, out->p, kModeFwd, nullptr, nullptr));
+        TRY(prop_inject(S.P, S.dsrc, S.q_d, k, out->p, nullptr, nullptr));
+        cp = cc;
+        cc = out;
+      }
+      state = op.b;
+    } else if (op.kind == kCkStore) {
+      if (state != op.a) return fail(WP_ECUDA, "internal error: checkpoint schedule out of order");
+      CU(cudaMemcpyAsync(sp[size_t(op.slot)].p, cp->p, G.field_bytes(), cudaMemcpyDeviceToDevice, c->stream));
+      CU(cudaMemcpyAsync(sc[size_t(op.slot)].p, cc->p, G.field_bytes(), cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+      if (state != op.a) return fail(WP_ECUDA, "internal error: checkpoint schedule out of order");
+      Field3 &w1 = A[kadj & 1], &w2 = A[(kadj + 1) & 1];
+      TRY(prop_step(S.P, w1, w2, w2.p, kModeAdjGrad, cc, &g));
+      TRY(prop_inject(S.P, S.drec, S.r_d, op.a - 1, w2.p, g.p, cc->p));
+      ++kadj;
+    }
+  }
+  TRY(grad_copy_out(c, G, g, grad_out, host_io));
+  return ctx_wait(c, "checkpointed gradient");
+}
+
+// ---------------------------------------------------------------------------
+// Boundary-wavefield reconstruction
+// ---------------------------------------------------------------------------
+// Where eta = 0 the update is symmetric in time: the forward step
+//     u^{n+1} = u^n + (u^n - u^{n-1}) + b L u^n + b P_s^T q^n
+// solved for u^{n-1} is the same expression with u^{n+1} and u^{n-1} swapped, so
+// the K1/K2 kernels run backward reproduce u^{n-1} on the box Z where eta = 0,
+// given u^n on Z and on the ring of width R around it (the Laplacian's reach).
+// The forward pass stores that ring for every level the backward pass rebuilds;
+// its end state (u^{nt-1}, u^nt) starts the reversal.  Values outside Z come out
+// wrong (the layer's damping is not reversible), so the gradient is returned on
+// Z and zero in the damping layer.
+
+// The box Z = {eta == 0}: bounding box of the zero points, verified to hold no
+// nonzero point.
+static int undamped_box(wp_ctx *c, const Geom &G, const float *eta_d, Box *Z) {
+  int *d = c->d_scalars + 8;  // 7 ints: bbox (6) + count
+  const int init[7] = {INT_MAX, -1, INT_MAX, -1, INT_MAX, -1, 0};
+  int *h = c->h_scalars + 8;
+  for (int i = 0; i < 7; ++i) h[i] = init[i];
+  CU(cudaMemcpyAsync(d, h, sizeof(init), cudaMemcpyHostToDevice, c->stream));
+  CU(launch_zero_bbox(c->stream, eta_d, G.fg(), d));
+  CU(cudaMemcpyAsync(h, d, 6 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  c->launches++;
+  TRY(ctx_wait(c, "undamped box"));
+  if (h[1] < 0) return fail(WP_EINVAL, "eta is nonzero everywhere: no undamped region to reconstruct");
+  *Z = Box{h[0], h[1] + 1, h[2], h[3] + 1, h[4], h[5] + 1};
+  CU(launch_count_nonzero(c->stream, eta_d, G.fg(), *Z, d + 6));
+  CU(cudaMemcpyAsync(h + 6, d + 6, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  c->launches++;
+  TRY(ctx_wait(c, "undamped box check"));
+  if (h[6]) return fail(WP_EINVAL, "the region where eta = 0 is not a box (%d nonzero points inside its bounds)", h[6]);
+  return WP_OK;
+}
+
+// The ring (Z grown by R along every axis longer than one point, clipped to the
+// grid) minus Z, as up to six boxes.
+static RingBoxes ring_boxes(const Geom &G, const Box &Z) {
+  const int rz = G.R, ry = G.ny > 1 ? G.R : 0, rx = G.R;
+  const Box E{std::max(Z.z0 - rz, 0), std::min(Z.z1 + rz, G.nz), std::max(Z.y0 - ry, 0), std::min(Z.y1 + ry, G.ny),
+              std::max(Z.x0 - rx, 0), std::min(Z.x1 + rx, G.nx)};
+  const Box cand[6] = {
+      {E.z0, Z.z0, E.y0, E.y1, E.x0, E.x1}, {Z.z1, E.z1, E.y0, E.y1, E.x0, E.x1},
+      {Z.z0, Z.z1, E.y0, Z.y0, E.x0, E.x1}, {Z.z0, Z.z1, Z.y1, E.y1, E.x0, E.x1},
+      {Z.z0, Z.z1, Z.y0, Z.y1, E.x0, Z.x0}, {Z.z0, Z.z1, Z.y0, Z.y1, Z.x1, E.x1},
+  };
+  RingBoxes rb;
+  std::memset(&rb, 0, sizeof(rb));
+  for (const Box &b : cand) {
+    const long long n = static_cast<long long>(b.z1 - b.z0) * (b.y1 - b.y0) * (b.x1 - b.x0);
+    if (b.z1 <= b.z0 || b.y1 <= b.y0 || b.x1 <= b.x0) continue;
+    rb.b[rb.n] = b;
+    rb.start[rb.n + 1] = rb.start[rb.n] + n;
+    ++rb.n;
+  }
+  return rb;
+}
+
+static int gradient_recon_impl(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta,
+                               const float *wavelet, int nsrc, const double *src, const float *residual, int nrec,
+                               const double *rec, float *grad_out, bool host_io) {
+  GradSetup S(c);
+  TRY(grad_setup(c, grid, m, eta, wavelet, nsrc, src, residual, nrec, rec, grad_out, host_io, S));
+  const Geom &G = S.G;
+  Arena &ar = S.ar;
+  Box Z;
+  TRY(undamped_box(c, G, S.eta_d, &Z));
+  const RingBoxes rb = ring_boxes(G, Z);
+  const long long nring = rb.start[rb.n];
+  const int nstore = std::max(G.nt - 2, 0);  // levels 1 .. nt-2
+  float *store = nullptr;
+  if (nring && nstore) TRY(ar.alloc(&store, size_t(nring) * nstore));
+  Field3 U[2], A[2], g;
+  TRY(alloc_field(ar, G, &U[0], true, c->stream));
+  TRY(alloc_field(ar, G, &U[1], true, c->stream));
+  TRY(alloc_field(ar, G, &A[0], true, c->stream));
+  TRY(alloc_field(ar, G, &A[1], true, c->stream));
+  TRY(alloc_field(ar, G, &g, true, c->stream));
+  // forward: (U[p], U[1-p]) = (u^{n-1}, u^n)
+  int p = 0;
+  for (int n = 0; n < G.nt; ++n) {
+    Field3 &prv = U[p], &cur = U[1 - p];
+    TRY(prop_step(S.P, cur, prv, prv.p, kModeFwd, nullptr, nullptr));
+    TRY(prop_inject(S.P, S.dsrc, S.q_d, n, prv.p, nullptr, nullptr));
+    p = 1 - p;  // prv now holds u^{n+1}
+    if (n + 1 <= nstore && nring) {
+      CU(launch_ring_copy(c->stream, prv.p, G.fg(), store + size_t(n) * nring, rb, true));
+      c->launches++;
+    }
+  }
+  // backward: lo = u^{j-1}, hi = u^j
+  Field3 *lo = &U[p], *hi = &U[1 - p];
+  long long kadj = 0;
+  for (int j = G.nt; j >= 1; --j, ++kadj) {
+    Field3 &w1 = A[kadj & 1], &w2 = A[(kadj + 1) & 1];
+    TRY(prop_step(S.P, w1, w2, w2.p, kModeAdjGrad, hi, &g));
+    TRY(prop_inject(S.P, S.drec, S.r_d, j - 1, w2.p, g.p, hi->p));
+    if (j >= 3) {
+      // u^{j-2} = u^{j-1} + (u^{j-1} - u^j) + b L u^{j-1} + b P_s^T q^{j-1} on Z, into hi
+      TRY(prop_step(S.P, *lo, *hi, hi->p, kModeFwd, nullptr, nullptr));
+      TRY(prop_inject(S.P, S.dsrc, S.q_d, j - 1, hi->p, nullptr, nullptr));
+      if (nring) {
+        CU(launch_ring_copy(c->stream, hi->p, G.fg(), store + size_t(j - 3) * nring, rb, false));
+        c->launches++;
+      }
+      std::swap(lo, hi);
+    } else {
+      hi = lo;
+    }
+  }
+  CU(launch_zero_outside(c->stream, g.p, G.fg(), Z));
+  c->launches++;
+  TRY(grad_copy_out(c, G, g, grad_out, host_io));
+  return ctx_wait(c, "gradient by boundary reconstruction");
+}
+
 int wp_forward_save(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *wavelet, int nsrc,
                     const double *src, int nrec, const double *rec, int S, float *rec_out, void *stream,
                     wp_state **state) {
@@ -1446,6 +1783,61 @@ int wp_fwi_gradient_dev(wp_ctx *c, const wp_grid *grid, const float *m, const fl
   TRY(enter(c, stream));
   return leave(c, stream,
                fwi_gradient_impl(c, grid, m, eta, wavelet, nsrc, src, d_obs, nrec, rec, S, grad_out, misfit, false));
+}
+
+int wp_gradient_checkpointed(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *wavelet,
+                             int nsrc, const double *src, const float *residual, int nrec, const double *rec,
+                             int checkpoints, float *grad_out) {
+  TRY(enter(c, nullptr));
+  return leave(c, nullptr, gradient_ckpt_impl(c, grid, m, eta, wavelet, nsrc, src, residual, nrec, rec, checkpoints,
+                                              grad_out, true));
+}
+
+int wp_gradient_checkpointed_dev(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta,
+                                 const float *wavelet, int nsrc, const double *src, const float *residual, int nrec,
+                                 const double *rec, int checkpoints, float *grad_out, void *stream) {
+  TRY(enter(c, stream));
+  return leave(c, stream, gradient_ckpt_impl(c, grid, m, eta, wavelet, nsrc, src, residual, nrec, rec, checkpoints,
+                                             grad_out, false));
+}
+
+int wp_gradient_reconstruct(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *wavelet,
+                            int nsrc, const double *src, const float *residual, int nrec, const double *rec,
+                            float *grad_out) {
+  TRY(enter(c, nullptr));
+  return leave(c, nullptr,
+               gradient_recon_impl(c, grid, m, eta, wavelet, nsrc, src, residual, nrec, rec, grad_out, true));
+}
+
+int wp_gradient_reconstruct_dev(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta,
+                                const float *wavelet, int nsrc, const double *src, const float *residual, int nrec,
+                                const double *rec, float *grad_out, void *stream) {
+  TRY(enter(c, stream));
+  return leave(c, stream,
+               gradient_recon_impl(c, grid, m, eta, wavelet, nsrc, src, residual, nrec, rec, grad_out, false));
+}
+
+int wp_checkpoint_schedule(int nt, int checkpoints, int *ops, int max_ops, int *nops, long long *forward_steps) {
+  if (nt < 0 || checkpoints < 0 || checkpoints > 4096 || !nops) return fail(WP_EINVAL, "bad schedule arguments");
+  CkTable tb;
+  ck_build(tb, nt, checkpoints);
+  std::vector<CkOp> v;
+  ck_schedule(tb, v);
+  *nops = static_cast<int>(v.size());
+  long long fw = 0;
+  for (const CkOp &op : v)
+    if (op.kind == kCkAdvance) fw += op.b - op.a;
+  if (forward_steps) *forward_steps = fw;
+  if (ops) {
+    if (max_ops < static_cast<int>(v.size())) return fail(WP_EINVAL, "ops holds %d entries, %zu needed", max_ops, v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+      ops[4 * i] = v[i].kind;
+      ops[4 * i + 1] = v[i].a;
+      ops[4 * i + 2] = v[i].b;
+      ops[4 * i + 3] = v[i].slot;
+    }
+  }
+  return WP_OK;
 }
 
 int wp_axpy_dev(wp_ctx *c, long long n, float alpha, const float *x, float *y, void *stream) {

@@ -1,5 +1,6 @@
 // 2D stencil (K1 in 2D), coefficient setup (A1), injection (K2), interpolation
 // (K3) and input checks.
+#include <limits.h>
 #include <math.h>
 
 #include "kernels.cuh"
@@ -162,6 +163,123 @@ cudaError_t launch_check_finite(cudaStream_t st, const float *x, long long n, in
   long long blocks = (n + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   check_finite_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(x, n, bad);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Boundary-wavefield reconstruction helpers: the box where eta vanishes, the
+// ring of stored boundary values around it, and the mask of the gradient.
+// ---------------------------------------------------------------------------
+__global__ void zero_bbox_kernel(const float *eta, FieldGeom g, int *box) {
+  const long long n = static_cast<long long>(g.nz) * g.ny * g.nx;
+  int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {-1, -1, -1};
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    if (eta[i] != 0.f) continue;
+    const int x = static_cast<int>(i % g.nx);
+    const long long zy = i / g.nx;
+    const int y = static_cast<int>(zy % g.ny);
+    const int z = static_cast<int>(zy / g.ny);
+    const int c[3] = {z, y, x};
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = min(lo[a], c[a]);
+      hi[a] = max(hi[a], c[a]);
+    }
+  }
+  for (int a = 0; a < 3; ++a) {
+    const int l = __reduce_min_sync(0xffffffffu, lo[a]);
+    const int h = __reduce_max_sync(0xffffffffu, hi[a]);
+    if ((threadIdx.x & 31) == 0 && h >= 0) {
+      atomicMin(box + 2 * a, l);
+      atomicMax(box + 2 * a + 1, h);
+    }
+  }
+}
+
+cudaError_t launch_zero_bbox(cudaStream_t st, const float *eta, FieldGeom g, int *box) {
+  const long long n = static_cast<long long>(g.nz) * g.ny * g.nx;
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  zero_bbox_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(eta, g, box);
+  return cudaGetLastError();
+}
+
+__global__ void count_nonzero_kernel(const float *eta, FieldGeom g, Box b, int *count) {
+  const int bx = b.x1 - b.x0, by = b.y1 - b.y0;
+  const long long n = static_cast<long long>(b.z1 - b.z0) * by * bx;
+  unsigned c = 0;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int x = b.x0 + static_cast<int>(i % bx);
+    const long long zy = i / bx;
+    const int y = b.y0 + static_cast<int>(zy % by);
+    const int z = b.z0 + static_cast<int>(zy / by);
+    c += eta[(static_cast<long long>(z) * g.ny + y) * g.nx + x] != 0.f;
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, static_cast<int>(c));
+}
+
+cudaError_t launch_count_nonzero(cudaStream_t st, const float *eta, FieldGeom g, Box b, int *count) {
+  const long long n = static_cast<long long>(b.z1 - b.z0) * (b.y1 - b.y0) * (b.x1 - b.x0);
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  count_nonzero_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(eta, g, b, count);
+  return cudaGetLastError();
+}
+
+__global__ void ring_copy_kernel(float *field, FieldGeom g, float *buf, RingBoxes rb, int to_buffer) {
+  const long long n = rb.start[rb.n];
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    int k = 0;
+    while (i >= rb.start[k + 1]) ++k;
+    const Box b = rb.b[k];
+    const long long l = i - rb.start[k];
+    const int bx = b.x1 - b.x0, by = b.y1 - b.y0;
+    const int x = b.x0 + static_cast<int>(l % bx);
+    const long long zy = l / bx;
+    const int y = b.y0 + static_cast<int>(zy % by);
+    const int z = b.z0 + static_cast<int>(zy / by);
+    const long long f = z * g.plane + static_cast<long long>(y) * g.pitch + x;
+    if (to_buffer)
+      buf[i] = field[f];
+    else
+      field[f] = buf[i];
+  }
+}
+
+cudaError_t launch_ring_copy(cudaStream_t st, float *field, FieldGeom g, float *buf, const RingBoxes &rb,
+                             bool to_buffer) {
+  const long long n = rb.start[rb.n];
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  ring_copy_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(field, g, buf, rb, to_buffer ? 1 : 0);
+  return cudaGetLastError();
+}
+
+__global__ void zero_outside_kernel(float *field, FieldGeom g, Box b) {
+  const long long n = static_cast<long long>(g.nz) * g.ny * g.nx;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(i % g.nx);
+    const long long zy = i / g.nx;
+    const int y = static_cast<int>(zy % g.ny);
+    const int z = static_cast<int>(zy / g.ny);
+    if (z < b.z0 || z >= b.z1 || y < b.y0 || y >= b.y1 || x < b.x0 || x >= b.x1)
+      field[z * g.plane + static_cast<long long>(y) * g.pitch + x] = 0.f;
+  }
+}
+
+cudaError_t launch_zero_outside(cudaStream_t st, float *field, FieldGeom g, Box b) {
+  const long long n = static_cast<long long>(g.nz) * g.ny * g.nx;
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  zero_outside_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(field, g, b);
   return cudaGetLastError();
 }
 

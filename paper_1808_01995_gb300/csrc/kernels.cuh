@@ -111,6 +111,29 @@ cudaError_t launch_axpy(cudaStream_t st, long long n, float alpha, const float *
 cudaError_t launch_update_model(cudaStream_t st, long long n, float step, const float *g, float *m, float lo,
                                 float hi);
 
+// ---- boundary-wavefield reconstruction (kernels.cu) ----
+// An axis-aligned box of grid points, [z0, z1) x [y0, y1) x [x0, x1).
+struct Box {
+  int z0, z1, y0, y1, x0, x1;
+};
+// box[0..5] = (min z, max z, min y, max y, min x, max x) over the points of the
+// contiguous field eta (nz, ny, nx) where eta == 0; box must hold
+// (INT_MAX, -1, INT_MAX, -1, INT_MAX, -1) on entry.
+cudaError_t launch_zero_bbox(cudaStream_t st, const float *eta, FieldGeom g, int *box);
+// *count += number of points inside `b` where eta != 0
+cudaError_t launch_count_nonzero(cudaStream_t st, const float *eta, FieldGeom g, Box b, int *count);
+// Up to six boxes of a pitched field, concatenated in order (each in z, y, x order)
+// in a contiguous buffer: gather (to_buffer) or scatter back.
+struct RingBoxes {
+  int n;
+  Box b[6];
+  long long start[7];  // prefix sums of the box sizes
+};
+cudaError_t launch_ring_copy(cudaStream_t st, float *field, FieldGeom g, float *buf, const RingBoxes &rb,
+                             bool to_buffer);
+// field = 0 at every point outside `b` (pitched field)
+cudaError_t launch_zero_outside(cudaStream_t st, float *field, FieldGeom g, Box b);
+
 // bit 0 of *bad set if any of x[0..n) is NaN or Inf
 cudaError_t launch_check_finite(cudaStream_t st, const float *x, long long n, int *bad);
 

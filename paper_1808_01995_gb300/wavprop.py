@@ -30,7 +30,8 @@ EXPORTED = [
     "wp_gradient_dev", "wp_propagate_dev", "wp_forward_save", "wp_backward", "wp_state_free",
     "wp_bytes_in_use", "wp_kernel_launches", "wp_set_profiling", "wp_profile_read",
     "wp_fwi_gradient", "wp_fwi_gradient_dev", "wp_trim", "wp_set_budget", "wp_axpy_dev",
-    "wp_update_model_dev",
+    "wp_update_model_dev", "wp_gradient_checkpointed", "wp_gradient_checkpointed_dev", "wp_checkpoint_schedule",
+    "wp_gradient_reconstruct", "wp_gradient_reconstruct_dev",
 ]
 
 
@@ -127,6 +128,11 @@ def lib() -> ctypes.CDLL:
         "wp_trim": ([_vp, ctypes.c_size_t], _i),
         "wp_set_budget": ([_vp, ctypes.c_size_t], _i),
         "wp_axpy_dev": ([_vp, ctypes.c_longlong, ctypes.c_float, _fp, _fp, _vp], _i),
+        "wp_gradient_checkpointed": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _fp, _i, _dp, _i, _fp], _i),
+        "wp_gradient_checkpointed_dev": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _fp, _i, _dp, _i, _fp, _vp], _i),
+        "wp_gradient_reconstruct": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _fp, _i, _dp, _fp], _i),
+        "wp_gradient_reconstruct_dev": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _fp, _i, _dp, _fp, _vp], _i),
+        "wp_checkpoint_schedule": ([_i, _i, _vp, _i, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_longlong)], _i),
         "wp_update_model_dev": ([_vp, ctypes.c_longlong, ctypes.c_float, _fp, _fp, ctypes.c_float, ctypes.c_float,
                                  _vp], _i),
     }
@@ -371,6 +377,70 @@ def wp_fwi_gradient_dev(ctx: int, grid: Grid, m, eta, wavelet, src, d_obs, rec, 
                                      int(snap_interval), _ptr(_dev_f32(grad_out, "grad_out")), ctypes.byref(J),
                                      _stream(stream)))
     return J.value
+
+
+def wp_gradient_checkpointed(ctx: int, grid: Grid, m, eta, wavelet, src, residual, rec,
+                             checkpoints: int) -> np.ndarray:
+    """wp_gradient with binomial checkpointing (`checkpoints` stored states)."""
+    m = _host_f32(m, grid.shape)
+    eta = _host_f32(eta, grid.shape)
+    src = _coords(src, grid.ndim)
+    rec = _coords(rec, grid.ndim)
+    q = _host_f32(wavelet, (grid.nt, len(src)))
+    r = _host_f32(residual, (grid.nt, len(rec)))
+    out = np.zeros(grid.shape, dtype=np.float32)
+    g = grid.c()
+    _check(lib().wp_gradient_checkpointed(ctx, ctypes.byref(g), _ptr(m), _ptr(eta), _ptr(q), len(src), _ptr(src),
+                                          _ptr(r), len(rec), _ptr(rec), int(checkpoints), _ptr(out)))
+    return out
+
+
+def wp_gradient_checkpointed_dev(ctx: int, grid: Grid, m, eta, wavelet, src, residual, rec, checkpoints: int,
+                                 grad_out, stream=None) -> None:
+    src = _coords(src, grid.ndim)
+    rec = _coords(rec, grid.ndim)
+    g = grid.c()
+    _check(lib().wp_gradient_checkpointed_dev(ctx, ctypes.byref(g), _ptr(_dev_f32(m, "m")),
+                                              _ptr(_dev_f32(eta, "eta")), _ptr(wavelet), len(src), _ptr(src),
+                                              _ptr(residual), len(rec), _ptr(rec), int(checkpoints),
+                                              _ptr(_dev_f32(grad_out, "grad_out")), _stream(stream)))
+
+
+def wp_gradient_reconstruct(ctx: int, grid: Grid, m, eta, wavelet, src, residual, rec) -> np.ndarray:
+    """Gradient by boundary-wavefield reconstruction (zero in the damping layer)."""
+    m = _host_f32(m, grid.shape)
+    eta = _host_f32(eta, grid.shape)
+    src = _coords(src, grid.ndim)
+    rec = _coords(rec, grid.ndim)
+    q = _host_f32(wavelet, (grid.nt, len(src)))
+    r = _host_f32(residual, (grid.nt, len(rec)))
+    out = np.zeros(grid.shape, dtype=np.float32)
+    g = grid.c()
+    _check(lib().wp_gradient_reconstruct(ctx, ctypes.byref(g), _ptr(m), _ptr(eta), _ptr(q), len(src), _ptr(src),
+                                         _ptr(r), len(rec), _ptr(rec), _ptr(out)))
+    return out
+
+
+def wp_gradient_reconstruct_dev(ctx: int, grid: Grid, m, eta, wavelet, src, residual, rec, grad_out,
+                                stream=None) -> None:
+    src = _coords(src, grid.ndim)
+    rec = _coords(rec, grid.ndim)
+    g = grid.c()
+    _check(lib().wp_gradient_reconstruct_dev(ctx, ctypes.byref(g), _ptr(_dev_f32(m, "m")),
+                                             _ptr(_dev_f32(eta, "eta")), _ptr(wavelet), len(src), _ptr(src),
+                                             _ptr(residual), len(rec), _ptr(rec),
+                                             _ptr(_dev_f32(grad_out, "grad_out")), _stream(stream)))
+
+
+def wp_checkpoint_schedule(nt: int, checkpoints: int):
+    """(ops as an (n, 4) int array of (kind, a, b, slot), recomputed forward steps)."""
+    n = ctypes.c_int()
+    fw = ctypes.c_longlong()
+    _check(lib().wp_checkpoint_schedule(int(nt), int(checkpoints), None, 0, ctypes.byref(n), ctypes.byref(fw)))
+    ops = np.zeros((n.value, 4), dtype=np.int32)
+    _check(lib().wp_checkpoint_schedule(int(nt), int(checkpoints), ops.ctypes.data if n.value else None, n.value,
+                                        ctypes.byref(n), ctypes.byref(fw)))
+    return ops, int(fw.value)
 
 
 def wp_trim(ctx: int, keep_bytes: int = 0) -> None:
