@@ -43,7 +43,16 @@ def zero_box(eta):
 
 
 def case(shape, k, nt, seed, nbl=6):
+    """Random model with its sources and receivers moved off-grid into the physical
+    domain (inside the box where eta = 0): a source inside the damping layer makes
+    the ring's values many orders larger than the field inside the box, and the
+    FP32 rounding of the reversal then swamps the small gradient there."""
     true = synth.random_case(shape, k, nsrc=2, nrec=19, nbl=nbl, seed=seed, vmin=1800, vmax=2600)
+    rng = np.random.default_rng(seed + 3)
+    lo = np.array(true.origin) + nbl * np.array(true.spacing)
+    hi = np.array(true.origin) + (np.array(shape) - nbl - 1) * np.array(true.spacing)
+    true.src = lo + rng.random((2, len(shape))) * (hi - lo)
+    true.rec = lo + rng.random((19, len(shape))) * (hi - lo)
     dt = 0.85 * O.cfl_dt(true.spacing, k, true.vmax)
     og = O.Grid(true.shape, true.spacing, true.origin, k, dt, nt)
     wg = W.Grid(true.shape, true.spacing, true.origin, k, dt, nt)
@@ -100,7 +109,7 @@ def test_reconstruction_rejects_eta_without_a_zero_box(ctx):
     true, og, wg, q, r = case((20, 22, 24), 4, 20, 5)
     m, e = true.m32(), true.eta32()
     e_all = np.full_like(e, 1e-4) * m
-    with pytest.raises(W.WpError, match="nowhere"):
+    with pytest.raises(W.WpError, match="nonzero everywhere"):
         W.wp_gradient_reconstruct(ctx.handle, wg, m, e_all, q, true.src, r, true.rec)
     e_hole = e.copy()
     Z = zero_box(e)
