@@ -60,6 +60,8 @@ def parse():
                    help="timed FWI gradients of the 200^3 + 40 blobs workload (0 skips the gradient leg)")
     p.add_argument("--checkpoints", type=int, default=20,
                    help="stored states of the binomial-checkpointing gradient timed beside it (0 skips it)")
+    p.add_argument("--no-full-history", dest="full_history", action="store_false",
+                   help="skip the full-history gradient (snap_interval 1, ~135 GB) timed beside the snapshot one")
     p.add_argument("--no-reconstruct", dest="reconstruct", action="store_false",
                    help="skip the boundary-reconstruction gradient timed beside the snapshot one")
     p.add_argument("--profile-every", type=int, default=10,
@@ -381,6 +383,20 @@ def gradient_leg(args):
               "device_bytes": int(W.wp_bytes_in_use(cctx.handle)), "forward_steps": fw,
               "same_as_snapshots": bool(torch.equal(gc, g))}
         cctx.close()
+    fh = {}
+    if args.full_history:
+        hctx = W.Context(0)
+        gh = torch.empty_like(m0)
+        W.wp_fwi_gradient_dev(hctx.handle, grid, m0, eta, q, true.src, d_obs, true.rec, 1, gh)
+        torch.cuda.synchronize()
+        e0.record()
+        W.wp_fwi_gradient_dev(hctx.handle, grid, m0, eta, q, true.src, d_obs, true.rec, 1, gh)
+        e1.record()
+        torch.cuda.synchronize()
+        fh = {"ms_per_gradient": e0.elapsed_time(e1), "device_bytes": int(W.wp_bytes_in_use(hctx.handle)),
+              "same_as_snapshots": bool(torch.equal(gh, g)),
+              "passes": "forward writing every level once + adjoint with fused correlation (no recompute)"}
+        hctx.close()
     rc = {}
     if args.reconstruct:
         rctx = W.Context(0)
@@ -401,7 +417,7 @@ def gradient_leg(args):
                         f"{len(true.rec)} receivers", "ms_per_gradient": ms,
             "gpts_per_s": npts * nt / (ms * 1e-3) / 1e9, "misfit": J, "device_bytes": int(peak),
             "passes": "forward with snapshots + recompute + adjoint with fused correlation",
-            "binomial_checkpointing": ck, "boundary_reconstruction": rc}
+            "full_history": fh, "binomial_checkpointing": ck, "boundary_reconstruction": rc}
 
 
 def run_ours(args):

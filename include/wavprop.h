@@ -126,7 +126,9 @@ int wp_adjoint(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *et
  *   grad = -dt^-2 sum_{j=1}^{nt} u^j (w^j - 2 w^{j+1} + w^{j+2}),
  * w the adjoint field driven by the residual.  The forward field is kept as
  * snapshot pairs every snap_interval steps in device memory and recomputed
- * between them (Sec. 3.3, checkpointing).  grad_out has the field's shape. */
+ * between them (Sec. 3.3, checkpointing); snap_interval = 1 keeps the whole
+ * history instead (each level stored once, nt fields, written by the forward
+ * step itself) and recomputes nothing.  grad_out has the field's shape. */
 int wp_gradient(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *eta,
                 const float *wavelet, int nsrc, const double *src_coords,
                 const float *residual, int nrec, const double *rec_coords, int snap_interval,

@@ -1035,8 +1035,9 @@ struct wp_state {
   Geom G;
   Prop P;
   std::vector<void *> mem;     // device blocks owned by the state
-  float *snaps = nullptr;      // [nseg][2][nfield]: (u^{sS-1}, u^{sS})
+  float *snaps = nullptr;      // [nseg][2][nfield]: (u^{sS-1}, u^{sS}); S = 1: [nt][nfield] = u^1..u^nt
   int S = 0, nseg = 0;
+  std::vector<Field3> hist;    // S = 1: level j (1..nt) at hist[j-1], with its own descriptors
   PointSet psrc, prec;
   DevPoints dsrc, drec;
   float *wavelet = nullptr;    // [nt][nsrc] device copy
@@ -1100,14 +1101,33 @@ static int forward_save(wp_ctx *c, const wp_grid *grid, const float *m, const fl
         if (c->h_scalars[1]) return fail(WP_ENONFINITE, "wavelet holds NaN or Inf");
       }
     }
-    if (st->nseg > 0) TRY(keep.alloc(&st->snaps, size_t(st->nseg) * 2 * G.nfield));
+    // S = 1 keeps the whole history once (each level written in place of a copy);
+    // otherwise snapshot pairs every S steps
+    if (st->S == 1 && G.nt > 0) {
+      TRY(keep.alloc(&st->snaps, size_t(G.nt) * G.nfield));
+      st->hist.resize(size_t(G.nt));
+      for (int j = 0; j < G.nt; ++j) {
+        st->hist[size_t(j)].p = st->snaps + size_t(j) * G.nfield;
+        TRY(make_field_maps(&st->hist[size_t(j)], G));
+      }
+    } else if (st->nseg > 0) {
+      TRY(keep.alloc(&st->snaps, size_t(st->nseg) * 2 * G.nfield));
+    }
     float *rec_d = nullptr;
     if (rec_out && n_out) {
       if (host_rec) TRY(tmp.alloc(&rec_d, n_out));
       else rec_d = rec_out;
     }
     Prop &P = st->P;
-    for (int n = 0; n < G.nt; ++n) {
+    // level k of the full history: u^{-1}, u^0 in the zeroed work fields
+    auto lev = [&](int k) -> Field3 & { return k == -1 ? u[0] : k == 0 ? u[1] : st->hist[size_t(k - 1)]; };
+    for (int n = 0; st->S == 1 && n < G.nt; ++n) {
+      Field3 &nxt = lev(n + 1);
+      TRY(prop_step(P, lev(n), lev(n - 1), nxt.p, kModeFwd, nullptr, nullptr));
+      TRY(prop_inject(P, st->dsrc, st->wavelet, n, nxt.p, nullptr, nullptr));
+      if (rec_d) TRY(prop_sample(P, st->drec, nxt.p, rec_d, n));
+    }
+    for (int n = 0; st->S > 1 && n < G.nt; ++n) {
       Field3 &cur = u[n & 1], &prv = u[(n + 1) & 1];
       if (n % st->S == 0) {
         float *dst = st->snaps + size_t(n / st->S) * 2 * G.nfield;
@@ -1162,6 +1182,22 @@ static int backward(wp_state *st, const float *residual, float *grad_out, bool h
     }
   }
   const int S = st->S;
+  if (S == 1) {  // full history: no recomputation
+    Field3 w[2], g;
+    TRY(alloc_field(tmp, G, &w[0], true, c->stream));
+    TRY(alloc_field(tmp, G, &w[1], true, c->stream));
+    TRY(alloc_field(tmp, G, &g, true, c->stream));
+    for (long long j = G.nt, kadj = 0; j >= 1; --j, ++kadj) {
+      Field3 &w1 = w[kadj & 1], &w2 = w[(kadj + 1) & 1];
+      const Field3 &uj = st->hist[size_t(j - 1)];
+      TRY(prop_step(P, w1, w2, w2.p, kModeAdjGrad, &uj, &g));
+      TRY(prop_inject(P, st->drec, res_d, int(j - 1), w2.p, g.p, uj.p));
+    }
+    CU(cudaMemcpy2DAsync(grad_out, size_t(G.nx) * 4, g.p, size_t(G.pitch) * 4, size_t(G.nx) * 4,
+                         size_t(G.ny) * G.nz, host_grad ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                         c->stream));
+    return ctx_wait(c, "backward (adjoint, gradient from the full history)");
+  }
   std::vector<Field3> ring(size_t(std::min(S, std::max(G.nt, 1))) + 2);
   for (auto &f : ring) TRY(alloc_field(tmp, G, &f, false, c->stream));
   Field3 w[2], g;
@@ -1394,7 +1430,9 @@ int wp_estimate_bytes(const wp_grid *grid, int nsrc, int nrec, int mode, int sna
   const size_t pts = size_t(nsrc + nrec) * 8 * 24 + size_t(G.nt) * (nsrc + nrec) * 4 * 2;
   const size_t flags = size_t(G.nz) * G.tiles_x * G.tiles_y;
   size_t b = 4 * f + pts + flags + (1 << 20);
-  if (mode == 1) {
+  if (mode == 1 && snap_interval <= 1) {
+    b += size_t(G.nt) * f + 3 * f;  // full history + adjoint + gradient
+  } else if (mode == 1) {
     const int S = std::max(snap_interval, 1);
     const size_t nseg = (size_t(G.nt) + S - 1) / S;
     b += 2 * nseg * f + size_t(std::min(S, std::max(G.nt, 1)) + 2 + 3) * f;

@@ -104,3 +104,31 @@ def test_checkpointed_gradient_large_model_matches_periodic(ctx):
     assert np.abs(g_per).max() > 0
     assert np.array_equal(g_ck, g_per)
     assert math.isfinite(float(np.abs(g_ck).sum()))
+
+
+@pytest.mark.parametrize("shape,k,nt", [((26, 29, 33), 8, 60), ((45, 51), 4, 120)])
+def test_full_history_gradient_equals_snapshot_gradient(ctx, shape, k, nt):
+    """snap_interval = 1 keeps every level once and recomputes nothing: the
+    forward levels are the same kernel outputs, so the gradient is bit-identical."""
+    true, og, wg, q, r = case(shape, k, nt, 37)
+    m, e = true.m32(), true.eta32()
+    g1 = W.wp_gradient(ctx.handle, wg, m, e, q, true.src, r, true.rec, 1)
+    g7 = W.wp_gradient(ctx.handle, wg, m, e, q, true.src, r, true.rec, 7)
+    assert np.abs(g1).max() > 0
+    assert np.array_equal(g1, g7)
+
+
+def test_full_history_autograd_and_receivers(ctx):
+    from paper_1808_01995_gb300.autograd import AcousticPropagator, misfit
+    true, og, wg, q, r = case((22, 27, 25), 4, 40, 43)
+    m0, e = true.m32(), true.eta32()
+    d_ref = W.wp_forward(ctx.handle, wg, m0, e, q, true.src, true.rec)
+    grads = []
+    for S in (1, 6):
+        prop = AcousticPropagator(true.shape, true.spacing, true.origin, 4, wg.dt, wg.nt, true.src, true.rec, S, ctx)
+        m = torch.from_numpy(m0).cuda().requires_grad_(True)
+        d = prop(m, torch.from_numpy(e).cuda(), torch.from_numpy(q).cuda())
+        assert np.array_equal(d.detach().cpu().numpy(), d_ref)
+        misfit(d, torch.zeros_like(d)).backward()
+        grads.append(m.grad.cpu().numpy())
+    assert np.array_equal(grads[0], grads[1])
