@@ -101,7 +101,8 @@ int wp_cfl_dt(const wp_grid *grid, double vmax, double *dt_max);
 /* Device bytes a call would hold for this grid: mode 0 forward/adjoint,
  * 1 gradient with the given snapshot interval, 2 checkpointed gradient with
  * snap_interval stored states, 3 gradient by boundary reconstruction (an upper
- * bound; snap_interval unused). */
+ * bound; snap_interval unused).  Temporal blocking (wp_set_temporal_blocking)
+ * adds two fields to mode 0. */
 int wp_estimate_bytes(const wp_grid *grid, int nsrc, int nrec, int mode, int snap_interval,
                       size_t *bytes);
 
@@ -242,6 +243,16 @@ int wp_forward_save(wp_ctx *ctx, const wp_grid *grid, const float *m, const floa
                     wp_state **state);
 int wp_backward(wp_state *state, const float *residual, float *grad_out, void *stream);
 void wp_state_free(wp_state *state);
+
+/* With enable != 0, forward (and few-receiver adjoint) time loops of 3D grids
+ * with space order <= 8 and at most 64 injection targets take two time steps
+ * per stencil launch (temporal blocking: u^{n+1} stays on chip for the second
+ * step, two extra wavefields); results are identical either way.  Default off
+ * (on if WP_TEMPORAL_BLOCKING=1 is set when the context is created): on GB300
+ * the two-step kernel is slower than two single steps (it is latency-bound at
+ * one CTA per SM).  No counterpart in the paper, which blocks loops in space
+ * only. */
+int wp_set_temporal_blocking(wp_ctx *ctx, int enable);
 
 /* Device bytes currently held by the context (including live states). */
 size_t wp_bytes_in_use(const wp_ctx *ctx);

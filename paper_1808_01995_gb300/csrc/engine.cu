@@ -22,6 +22,7 @@
 #include "../../include/wavprop.h"
 #include "kernels.cuh"
 #include "stencil3d.cuh"
+#include "stencil3d_tb.cuh"
 
 using namespace wp;
 
@@ -71,6 +72,8 @@ struct wp_ctx {
   int smem3d[2][9] = {};
   int occ3d[2][9] = {};
   int ty3d[2][9] = {};
+  int smem_tb[5] = {}, occ_tb[5] = {};     // two-step kernel, half-orders 1..4
+  bool temporal_blocking = false;         // forward loops take two steps per stencil launch
   bool broken = false;
   // profiling: an event pair around every prof_every-th stencil launch, summed on read
   bool profiling = false;
@@ -479,6 +482,8 @@ struct Field3 {
   float *p = nullptr;
   bool mapped = false;  // descriptors encoded for p
   CUtensorMap halo[2], tile[2];
+  bool tb_mapped = false;  // two-step kernel: [0] u^n plane box, [1] region box, [2] core box
+  CUtensorMap tb[3];
 };
 
 static int make_field_maps(Field3 *f, const Geom &G) {
@@ -489,6 +494,13 @@ static int make_field_maps(Field3 *f, const Geom &G) {
     TRY(make_map(&f->tile[mode], f->p, G, tx, ty));
   }
   f->mapped = true;
+  TbShape sh;
+  if (stencil3d_tb_shape(G.R, &sh)) {
+    TRY(make_map(&f->tb[0], f->p, G, sh.plane_w, sh.plane_h));
+    TRY(make_map(&f->tb[1], f->p, G, sh.region_w, sh.region_h));
+    TRY(make_map(&f->tb[2], f->p, G, sh.core_w, sh.core_h));
+    f->tb_mapped = true;
+  }
   return WP_OK;
 }
 
@@ -500,9 +512,9 @@ struct Plan3d {
   dim3 grid;
 };
 
-static Plan3d plan3d(const Geom &G, int mode, int num_sms, int occ) {
+// tx x ty tiles; every item streams its chunk plus `extra` planes
+static Plan3d plan_items(const Geom &G, int tx, int ty, int extra, int num_sms, int occ) {
   Plan3d p;
-  const int tx = stencil3d_tile_x(G.R, mode), ty = stencil3d_tile_y(G.R, mode);
   p.tiles_x = (G.nx + tx - 1) / tx;
   p.tiles_y = (G.ny + ty - 1) / ty;
   const long long tiles = static_cast<long long>(p.tiles_x) * p.tiles_y;
@@ -517,7 +529,7 @@ static Plan3d plan3d(const Geom &G, int mode, int num_sms, int occ) {
     const long long rounds = (items + ctas - 1) / ctas;
     const double used = std::min(1.0, double(items) / double(ctas));
     // fewer CTAs than slots leave bandwidth unused: charge the idle fraction
-    const double cost = double(rounds) * (zc + G.R) / std::min(1.0, used / 0.9);
+    const double cost = double(rounds) * (zc + extra) / std::min(1.0, used / 0.9);
     if (cost < best * 0.999) {
       best = cost;
       p.zchunk = zc;
@@ -534,6 +546,10 @@ static Plan3d plan3d(const Geom &G, int mode, int num_sms, int occ) {
   return p;
 }
 
+static Plan3d plan3d(const Geom &G, int mode, int num_sms, int occ) {
+  return plan_items(G, stencil3d_tile_x(G.R, mode), stencil3d_tile_y(G.R, mode), G.R, num_sms, occ);
+}
+
 // ---------------------------------------------------------------------------
 // the propagator of one call: coefficients, launch configuration, step launches
 // ---------------------------------------------------------------------------
@@ -545,6 +561,9 @@ struct Prop {
   Field3 b, s;
   unsigned *tbits = nullptr;
   Plan3d plan[2];
+  bool tb = false;  // the two-step kernel covers this grid
+  Plan3d plan_tb;
+  uint2 *tb_bits = nullptr;  // [tile][nzw] damping words of the two-step tiles
 };
 
 static int prop_setup(wp_ctx *c, Arena &ar, const Geom &G, const float *m, const float *eta, Prop *P) {
@@ -595,6 +614,34 @@ static int prop_setup(wp_ctx *c, Arena &ar, const Geom &G, const float *m, const
     TRY(make_field_maps(&P->b, G));
     TRY(make_field_maps(&P->s, G));
     for (int mode = 0; mode < 2; ++mode) P->plan[mode] = plan3d(G, mode, c->num_sms, c->occ3d[mode][G.R]);
+    TbShape sh;
+    if (stencil3d_tb_shape(G.R, &sh) && c->occ_tb[G.R] > 0) {
+      P->tb = true;
+      P->plan_tb = plan_items(G, sh.core_w, sh.core_h, 2 * G.R, c->num_sms, c->occ_tb[G.R]);
+      const Plan3d &pt = P->plan_tb;
+      TRY(ar.alloc(&P->tb_bits, size_t(pt.tiles_x) * pt.tiles_y * G.nzw));
+      TbFlagArgs f;
+      memset(&f, 0, sizeof f);
+      f.tbits = P->tbits;
+      f.nzw = G.nzw;
+      f.flag_tiles_x = G.tiles_x;
+      f.flag_tiles_y = G.tiles_y;
+      f.flag_w = kFlagTX;
+      f.flag_h = kTileFlagTY;
+      f.nx = G.nx;
+      f.ny = G.ny;
+      f.tiles_x = pt.tiles_x;
+      f.tiles_y = pt.tiles_y;
+      f.core_w = sh.core_w;
+      f.core_h = sh.core_h;
+      f.rim_x = sh.rim_x;
+      f.rim_y = G.R;
+      f.region_w = sh.region_w;
+      f.region_h = sh.region_h;
+      f.out = P->tb_bits;
+      CU(launch_tb_flags(c->stream, f));
+      c->launches++;
+    }
   }
   return WP_OK;
 }
@@ -730,6 +777,60 @@ static int prop_step(Prop &P, const Field3 &u, const Field3 &um, float *out, int
   P.c->launches++;
   if (P.c->prof_open) TRY(prof_mark(P.c));
   if (!P.c->capturing && P.c->prof_used >= 4096) {  // bound the event pool: fold what has completed
+    TRY(ctx_wait(P.c));
+    TRY(prof_collect(P.c));
+  }
+  return WP_OK;
+}
+
+// Two forward steps in one launch: (u^{n-1}, u^n) = (um, u) -> (u^{n+1}, u^{n+2}) =
+// (out1, out2), with data row `row` (+ *row_base) of `inj` injected into u^{n+1};
+// the caller injects the next row into out2.
+static int prop_step2(Prop &P, const Field3 &um, const Field3 &u, Field3 &out1, Field3 &out2, const DevPoints &inj,
+                      const float *data, long long row, const long long *row_base) {
+  const Geom &G = P.G;
+  if (!P.tb || !um.tb_mapped || !u.tb_mapped || !P.b.tb_mapped || !P.s.tb_mapped)
+    return fail(WP_ECUDA, "internal error: a field of the two-step stencil has no TMA descriptor");
+  if (inj.ntarget > kTbMaxTargets) return fail(WP_ECUDA, "internal error: too many targets for the two-step stencil");
+  P.c->prof_open = P.c->profiling && (P.c->prof_seq++ % uint64_t(P.c->prof_every)) == 0;
+  if (P.c->prof_open) TRY(prof_mark(P.c));
+  const Plan3d &pl = P.plan_tb;
+  Stencil3dTbArgs a;
+  memset(&a, 0, sizeof a);
+  a.g = G.fg();
+  a.c = P.lc;
+  a.out1 = out1.p;
+  a.out2 = out2.p;
+  a.tile_bits = P.tb_bits;
+  a.nzw = G.nzw;
+  a.tiles_x = pl.tiles_x;
+  a.tiles_y = pl.tiles_y;
+  a.zchunk = pl.zchunk;
+  a.nzc = pl.nzc;
+  a.nitems = pl.nitems;
+  a.err = P.c->d_scalars;
+  a.ntarget = data ? inj.ntarget : 0;
+  a.target = inj.target;
+  a.rowptr = inj.rowptr;
+  a.pid = inj.pid;
+  a.w = inj.cw;
+  a.data = data;
+  a.npts = inj.npts;
+  a.row_base = row_base;
+  a.row = row;
+  a.b = P.b.p;
+  const CUtensorMap maps[6] = {u.tb[0], um.tb[1], P.b.tb[1], P.s.tb[1], P.b.tb[2], P.s.tb[2]};
+  if (P.c->hashing) {
+    hash_bytes(P.c, &a, sizeof a);
+    hash_bytes(P.c, maps, sizeof maps);
+    hash_bytes(P.c, &pl.grid, sizeof pl.grid);
+    return P.c->prof_open ? prof_mark(P.c) : WP_OK;
+  }
+  cudaError_t e = launch_stencil3d_tb(G.R, pl.grid, P.c->stream, maps, a);
+  if (e != cudaSuccess) return fail(WP_ECUDA, "two-step stencil launch failed: %s", cudaGetErrorString(e));
+  P.c->launches++;
+  if (P.c->prof_open) TRY(prof_mark(P.c));
+  if (!P.c->capturing && P.c->prof_used >= 4096) {
     TRY(ctx_wait(P.c));
     TRY(prof_collect(P.c));
   }
@@ -932,6 +1033,68 @@ static int run_loop(Prop &P, Field3 u[2], int nt, const DevPoints &inj, const fl
   return WP_OK;
 }
 
+// Whether the time loop can take two steps per launch (3D, the two-step kernel
+// covers the order, few enough injection targets, switched on).
+static bool two_step_ok(const Prop &P, const DevPoints &inj, int nt) {
+  return P.G.ndim == 3 && P.tb && P.c->temporal_blocking && inj.ntarget <= kTbMaxTargets && nt >= 2;
+}
+
+// The same time loop two steps per stencil launch, over four fields: the pair
+// (u[0], u[1]) = (u^{k-1}, u^k) steps into (u[2], u[3]) and back.  Each pair
+// launches the two-step kernel (row k injected inside), injects row k + 1 into
+// u^{k+2} and samples both levels; blocks of B steps (B a multiple of 4, so the
+// buffer parity repeats) are graph replays.  An odd last step runs single.
+static int run_loop2(Prop &P, Field3 u[4], int nt, const DevPoints &inj, const float *data, const DevPoints &smp,
+                     float *out, int dir) {
+  wp_ctx *c = P.c;
+  auto pair = [&](int j, long long ra, long long rb_, const long long *base) -> int {
+    Field3 &um = u[(j & 1) ? 2 : 0], &uc = u[(j & 1) ? 3 : 1];
+    Field3 &o1 = u[(j & 1) ? 0 : 2], &o2 = u[(j & 1) ? 1 : 3];
+    TRY(prop_step2(P, um, uc, o1, o2, inj, data, ra, base));
+    TRY(prop_inject(P, inj, data, rb_, o2.p, nullptr, nullptr, base));
+    if (out) {
+      TRY(prop_sample(P, smp, o1.p, out, ra, base));
+      TRY(prop_sample(P, smp, o2.p, out, rb_, base));
+    }
+    return WP_OK;
+  };
+  int k0 = 0;
+  int B = 0;
+  if (c->use_graphs && nt >= 16) {
+    int best_rem = nt;
+    for (int b = 64; b >= 8; b -= 4)
+      if (nt % b < best_rem) {
+        B = b;
+        best_rem = nt % b;
+      }
+  }
+  if (B > 0) {
+    long long *rb = c->d_rows;
+    CU(launch_set_row(c->stream, rb, dir > 0 ? 0 : nt - 1));
+    c->launches++;
+    auto block = [&]() -> int {
+      for (int j = 0; j < B / 2; ++j) TRY(pair(j, dir * 2 * j, dir * (2 * j + 1), rb));
+      return prop_add_row(c, rb, static_cast<long long>(dir) * B);
+    };
+    TRY(graph_replay(c, block, nt / B));
+    k0 = (nt / B) * B;
+  }
+  int k = k0;
+  for (; k + 2 <= nt; k += 2) {
+    const long long ra = dir > 0 ? k : nt - 1 - k, rb_ = dir > 0 ? k + 1 : nt - 2 - k;
+    TRY(pair(k / 2, ra, rb_, nullptr));
+  }
+  if (k < nt) {  // one step left: the pair parity says where (u^{k-1}, u^k) are
+    const long long row = dir > 0 ? k : nt - 1 - k;
+    const int j = k / 2;
+    Field3 &prv = u[(j & 1) ? 2 : 0], &cur = u[(j & 1) ? 3 : 1];
+    TRY(prop_step(P, cur, prv, prv.p, kModeFwd, nullptr, nullptr));
+    TRY(prop_inject(P, inj, data, row, prv.p, nullptr, nullptr));
+    if (out) TRY(prop_sample(P, smp, prv.p, out, row));
+  }
+  return WP_OK;
+}
+
 // ---------------------------------------------------------------------------
 // common call prologue
 // ---------------------------------------------------------------------------
@@ -1022,7 +1185,16 @@ static int do_propagate(wp_ctx *c, const wp_grid *grid, const float *m, const fl
     TRY(ctx_wait(c));
     if (c->h_scalars[1]) return fail(WP_ENONFINITE, "injected data holds NaN or Inf");
   }
-  TRY(run_loop(P, u, G.nt, din, data_d, dsm, n_out ? out_d : nullptr, dir));
+  if (two_step_ok(P, din, G.nt)) {
+    Field3 u4[4];
+    u4[0] = u[0];
+    u4[1] = u[1];
+    TRY(alloc_field(ar, G, &u4[2], false, c->stream));
+    TRY(alloc_field(ar, G, &u4[3], false, c->stream));
+    TRY(run_loop2(P, u4, G.nt, din, data_d, dsm, n_out ? out_d : nullptr, dir));
+  } else {
+    TRY(run_loop(P, u, G.nt, din, data_d, dsm, n_out ? out_d : nullptr, dir));
+  }
   if (host_io && n_out) CU(cudaMemcpyAsync(smp_out, out_d, n_out * 4, cudaMemcpyDeviceToHost, c->stream));
   return ctx_wait(c, dir > 0 ? "forward time loop" : "adjoint time loop");
 }
@@ -1349,6 +1521,9 @@ int wp_create(wp_ctx **out, int device, size_t budget) {
       CU(prepare_stencil3d_fwd(R, &c->smem3d[0][R], &c->occ3d[0][R], &c->ty3d[0][R]));
       CU(prepare_stencil3d_adj(R, &c->smem3d[1][R], &c->occ3d[1][R], &c->ty3d[1][R]));
     }
+    for (int R = 1; R <= 4; ++R) CU(prepare_stencil3d_tb(R, &c->smem_tb[R], &c->occ_tb[R]));
+    const char *tbe = getenv("WP_TEMPORAL_BLOCKING");
+    c->temporal_blocking = tbe && atoi(tbe) != 0;
     return WP_OK;
   }();
   if (rc != WP_OK) {
@@ -1380,6 +1555,12 @@ void wp_destroy(wp_ctx *c) {
 int wp_set_timeout(wp_ctx *c, double seconds) {
   if (!c || !(seconds > 0)) return fail(WP_EINVAL, "bad context or timeout");
   c->timeout_s = seconds;
+  return WP_OK;
+}
+
+int wp_set_temporal_blocking(wp_ctx *c, int enable) {
+  if (!c) return fail(WP_EINVAL, "context is NULL");
+  c->temporal_blocking = enable != 0;
   return WP_OK;
 }
 

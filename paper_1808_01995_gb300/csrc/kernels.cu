@@ -167,6 +167,41 @@ cudaError_t launch_check_finite(cudaStream_t st, const float *x, long long n, in
 }
 
 // ---------------------------------------------------------------------------
+// Damping words of the two-step stencil's tiles (one thread per tile and word)
+// ---------------------------------------------------------------------------
+__global__ void tb_flags_kernel(const TbFlagArgs a) {
+  const long long n = static_cast<long long>(a.tiles_x) * a.tiles_y * a.nzw;
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const int w = static_cast<int>(i % a.nzw);
+  const int tile = static_cast<int>(i / a.nzw);
+  const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+  const int gx0 = tx * a.core_w, gy0 = ty * a.core_h;
+  auto word = [&](int x0, int x1, int y0, int y1) -> unsigned {
+    x0 = max(x0, 0);
+    y0 = max(y0, 0);
+    x1 = min(x1, a.nx);
+    y1 = min(y1, a.ny);
+    unsigned m = 0;
+    if (x0 >= x1 || y0 >= y1) return 0u;
+    for (int fy = y0 / a.flag_h; fy <= (y1 - 1) / a.flag_h && fy < a.flag_tiles_y; ++fy)
+      for (int fx = x0 / a.flag_w; fx <= (x1 - 1) / a.flag_w && fx < a.flag_tiles_x; ++fx)
+        m |= a.tbits[(static_cast<long long>(fy) * a.flag_tiles_x + fx) * a.nzw + w];
+    return m;
+  };
+  const int rx0 = gx0 - a.rim_x, ry0 = gy0 - a.rim_y;
+  a.out[i] = make_uint2(word(rx0, rx0 + a.region_w, ry0, ry0 + a.region_h),
+                        word(gx0, gx0 + a.core_w, gy0, gy0 + a.core_h));
+}
+
+cudaError_t launch_tb_flags(cudaStream_t st, const TbFlagArgs &a) {
+  const long long n = static_cast<long long>(a.tiles_x) * a.tiles_y * a.nzw;
+  if (n <= 0) return cudaSuccess;
+  tb_flags_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Boundary-wavefield reconstruction helpers: the box where eta vanishes, the
 // ring of stored boundary values around it, and the mask of the gradient.
 // ---------------------------------------------------------------------------
@@ -297,8 +332,9 @@ __global__ void inject_kernel(const InjectArgs a) {
   float acc = 0.f;
   for (int k = a.rowptr[i]; k < a.rowptr[i + 1]; ++k) acc = fmaf(a.w[k], q[a.pid[k]], acc);
   const long long t = a.target[i];
-  const float inc = a.b[t] * acc;
-  a.u[t] += inc;
+  // explicit roundings (no contraction): the two-step stencil repeats this arithmetic
+  const float inc = __fmul_rn(a.b[t], acc);
+  a.u[t] = __fadd_rn(a.u[t], inc);
   if (a.grad) a.grad[t] = fmaf(a.neg_inv_dt2 * a.uj[t], inc, a.grad[t]);
 }
 

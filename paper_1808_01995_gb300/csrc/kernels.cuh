@@ -31,6 +31,33 @@ inline int stencil3d_tile_y(int R, int mode) {
   return mode == 1 ? stencil3d_tile_y_adj(R) : stencil3d_tile_y_fwd(R);
 }
 
+// ---- K1, 3D, two steps per launch (stencil3d_tb.cu) ----
+struct Stencil3dTbArgs;
+// Box sizes of the two-step kernel for half-order R (false if R is not covered).
+struct TbShape {
+  int region_w, region_h;  // step-1 region (u^{n-1}, b, s tiles)
+  int core_w, core_h;      // step-2 core (b, s tiles; output)
+  int rim_x;               // x offset of the core in the region (y offset: R)
+  int plane_w, plane_h;    // halo'd u^n plane box
+};
+bool stencil3d_tb_shape(int R, TbShape *s);
+// maps: u^n (plane box), u^{n-1}, b, s (region boxes), b, s (core boxes)
+cudaError_t launch_stencil3d_tb(int R, dim3 grid, cudaStream_t st, const CUtensorMap *maps,
+                                const Stencil3dTbArgs &a);
+cudaError_t prepare_stencil3d_tb(int R, int *smem_bytes, int *blocks_per_sm);
+
+// Damping words of the two-step kernel's tiles: out[tile][w] = (region word, core
+// word), the OR of the flag-tile bitmasks (bit z of word w: plane 32 w + z damped)
+// over the flag tiles that meet the tile's region / core box.
+struct TbFlagArgs {
+  const unsigned *tbits;
+  int nzw, flag_tiles_x, flag_tiles_y, flag_w, flag_h;
+  int nx, ny;
+  int tiles_x, tiles_y, core_w, core_h, rim_x, rim_y, region_w, region_h;
+  uint2 *out;
+};
+cudaError_t launch_tb_flags(cudaStream_t st, const TbFlagArgs &a);
+
 // ---- K1, 2D (kernels.cu) ----
 struct Stencil2dArgs {
   FieldGeom g;        // 2D fields use nz rows of `pitch` elements (ny = 1)

@@ -31,7 +31,7 @@ EXPORTED = [
     "wp_bytes_in_use", "wp_kernel_launches", "wp_set_profiling", "wp_profile_read",
     "wp_fwi_gradient", "wp_fwi_gradient_dev", "wp_trim", "wp_set_budget", "wp_axpy_dev",
     "wp_update_model_dev", "wp_gradient_checkpointed", "wp_gradient_checkpointed_dev", "wp_checkpoint_schedule",
-    "wp_gradient_reconstruct", "wp_gradient_reconstruct_dev",
+    "wp_gradient_reconstruct", "wp_gradient_reconstruct_dev", "wp_set_temporal_blocking",
 ]
 
 
@@ -130,6 +130,7 @@ def lib() -> ctypes.CDLL:
         "wp_axpy_dev": ([_vp, ctypes.c_longlong, ctypes.c_float, _fp, _fp, _vp], _i),
         "wp_gradient_checkpointed": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _fp, _i, _dp, _i, _fp], _i),
         "wp_gradient_checkpointed_dev": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _fp, _i, _dp, _i, _fp, _vp], _i),
+        "wp_set_temporal_blocking": ([_vp, _i], _i),
         "wp_gradient_reconstruct": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _fp, _i, _dp, _fp], _i),
         "wp_gradient_reconstruct_dev": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _fp, _i, _dp, _fp, _vp], _i),
         "wp_checkpoint_schedule": ([_i, _i, _vp, _i, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_longlong)], _i),
@@ -441,6 +442,10 @@ def wp_checkpoint_schedule(nt: int, checkpoints: int):
     _check(lib().wp_checkpoint_schedule(int(nt), int(checkpoints), ops.ctypes.data if n.value else None, n.value,
                                         ctypes.byref(n), ctypes.byref(fw)))
     return ops, int(fw.value)
+
+
+def wp_set_temporal_blocking(ctx: int, enable: bool) -> None:
+    _check(lib().wp_set_temporal_blocking(ctx, 1 if enable else 0))
 
 
 def wp_trim(ctx: int, keep_bytes: int = 0) -> None:
