@@ -63,6 +63,9 @@ enum StencilMode : int { kModeFwd = 0, kModeAdjGrad = 1 };
 #ifndef WP_ZU
 #define WP_ZU 2          // planes per unrolled z step (1..4)
 #endif
+#ifndef WP_P_ADJ
+#define WP_P_ADJ 2       // planes in flight, adjoint+gradient mode, R <= 4 (two CTAs per SM)
+#endif
 
 
 template <int R, int MODE>
@@ -75,7 +78,7 @@ struct Cfg3d {
   static constexpr int RE = (R + 1) / 2 * 2;                         // x window half-width (even)
   static constexpr int PW = TX + 2 * RX;
   static constexpr int PH = TY + 2 * R;
-  static constexpr int P = R <= 4 ? 3 : WP_P_HI;                     // planes in flight ahead
+  static constexpr int P = R > 4 ? WP_P_HI : MODE == kModeAdjGrad ? WP_P_ADJ : 3;  // planes in flight ahead
   static constexpr int MINB = R <= 4 ? WP_MINB_LO : WP_MINB_HI;      // CTAs per SM to fit
   static constexpr int ZU = WP_ZU;                                   // planes per unrolled z step
   static constexpr int NSU = R + 1 + P;                              // u ring depth
