@@ -34,7 +34,13 @@
 namespace wp {
 
 #ifndef WP_TB_NY
-#define WP_TB_NY 4       // rows per lane
+#define WP_TB_NY 4       // rows per lane, R > 2 (one CTA per SM)
+#endif
+#ifndef WP_TB_ZU
+#define WP_TB_ZU 1       // planes per unrolled z step (1 or 2; 1 measured faster: smaller code)
+#endif
+#ifndef WP_TB_NY_LO
+#define WP_TB_NY_LO 4    // rows per lane, R <= 2 (2: two CTAs per SM, measured slower)
 #endif
 
 constexpr int kTbMaxTargets = 64;  // injection targets handled inside the kernel
@@ -43,7 +49,8 @@ template <int R>
 struct CfgTb {
   static_assert(R >= 1 && R <= 4, "the two-step kernel covers space orders 2..8");
   static constexpr int NX = 2;
-  static constexpr int NY = WP_TB_NY;
+  static constexpr int NY = R <= 2 ? WP_TB_NY_LO : WP_TB_NY;
+  static constexpr int MINB = NY <= 2 ? 2 : 1;     // CTAs per SM the registers must allow
   static constexpr int W = 32 * NX;                // region width (step 1)
   static constexpr int H = kConsumerWarps * NY;    // region height
   static constexpr int RX = 4;                     // x rim, 16 bytes for TMA
@@ -53,7 +60,7 @@ struct CfgTb {
   static constexpr int UPW = W + 2 * RX;           // u^n plane box
   static constexpr int UPH = H + 2 * R;
   static constexpr int P = 2;                      // planes in flight ahead
-  static constexpr int ZU = 2;                     // planes per unrolled z step
+  static constexpr int ZU = WP_TB_ZU;              // planes per unrolled z step
   static constexpr int NSU = R + 1 + P;            // u^n ring depth
   static constexpr int NST = P + 1;                // region tile ring depth
   static constexpr int NSC = P + 1;                // core tile ring depth
@@ -101,7 +108,7 @@ constexpr int kThreadsTb = kConsumerWarps * 32;
 // tm: [0] u^n (plane box UPW x UPH), [1] u^{n-1}, [2] b, [3] s (region boxes W x H),
 //     [4] b, [5] s (core boxes CW x CH)
 template <int R>
-__global__ void __launch_bounds__(kThreadsTb, 1)
+__global__ void __launch_bounds__(kThreadsTb, CfgTb<R>::MINB)
     stencil3d_tb_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_um,
                         const __grid_constant__ CUtensorMap tm_b, const __grid_constant__ CUtensorMap tm_s,
                         const __grid_constant__ CUtensorMap tm_bc, const __grid_constant__ CUtensorMap tm_sc,
@@ -224,7 +231,7 @@ __global__ void __launch_bounds__(kThreadsTb, 1)
       }
       if (kind == 0) {
         const uint32_t slot = iu % C::NSU;
-        if (iu >= C::NSU && !mbar_try_wait(&empty_u[slot], ((iu / C::NSU) - 1) & 1)) return;
+        if (iu >= C::NSU && !mbar_test_wait(&empty_u[slot], ((iu / C::NSU) - 1) & 1)) return;
         float *dst = uring + slot * (C::USLOT / 4);
         if ((smem_u32(dst) & 127u) || ((rx0 - C::RX) & 3)) {
           fail_align();
@@ -235,7 +242,7 @@ __global__ void __launch_bounds__(kThreadsTb, 1)
         ++iu;
       } else if (kind == 1) {
         const uint32_t slot = itt % C::NST;
-        if (itt >= C::NST && !mbar_try_wait(&empty_t[slot], ((itt / C::NST) - 1) & 1)) return;
+        if (itt >= C::NST && !mbar_test_wait(&empty_t[slot], ((itt / C::NST) - 1) & 1)) return;
         float *t = tring + slot * (3 * TT);
         if ((smem_u32(t) & 127u) || (rx0 & 3)) {
           fail_align();
@@ -250,7 +257,7 @@ __global__ void __launch_bounds__(kThreadsTb, 1)
         ++itt;
       } else {
         const uint32_t slot = ic % C::NSC;
-        if (ic >= C::NSC && !mbar_try_wait(&empty_c[slot], ((ic / C::NSC) - 1) & 1)) return;
+        if (ic >= C::NSC && !mbar_test_wait(&empty_c[slot], ((ic / C::NSC) - 1) & 1)) return;
         float *t = cring + slot * (2 * CT);
         if ((smem_u32(t) & 127u) || (smem_u32(t + CT) & 127u) || (gx0 & 3)) {
           fail_align();
@@ -275,11 +282,12 @@ __global__ void __launch_bounds__(kThreadsTb, 1)
     }
   };
   // bounded wait on a full barrier; the producer lane issues loads while it waits
+  // and probes without suspending (test_wait)
   auto wait_full = [&](uint64_t *bar, uint32_t parity) {
     if (producer) {
       pump();
       const uint64_t t0 = global_timer_ns();
-      while (!mbar_try_wait(bar, parity)) {
+      while (!mbar_test_wait(bar, parity)) {
         if (*abort_flag) return;
         pump();
         if (global_timer_ns() - t0 > kWaitLimitNs) {
