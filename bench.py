@@ -58,6 +58,8 @@ def parse():
                    help="scale of the request sizes and nt (1.0 = 128..320 x 128..320 x 128..200 + 40, nt 500..2000)")
     p.add_argument("--gradient", type=int, default=3,
                    help="timed FWI gradients of the 200^3 + 40 blobs workload (0 skips the gradient leg)")
+    p.add_argument("--gradient-nt", type=int, default=1500,
+                   help="time steps of the gradient workload (1500; fewer only for profiling)")
     p.add_argument("--checkpoints", type=int, default=20,
                    help="stored states of the binomial-checkpointing gradient timed beside it (0 skips it)")
     p.add_argument("--no-full-history", dest="full_history", action="store_false",
@@ -341,7 +343,7 @@ def gradient_leg(args):
     from paper_1808_01995_gb300 import synth
     from paper_1808_01995_gb300 import wavprop as W
     true, start = synth.blobs_3d()
-    k, nt, S = 8, 1500, 10
+    k, nt, S = 8, args.gradient_nt, 10
     dt = 0.9 * W.wp_cfl_dt(W.Grid(true.shape, true.spacing, true.origin, k), max(true.vmax, start.vmax))
     grid = W.Grid(true.shape, true.spacing, true.origin, k, dt, nt)
     ctx = W.Context(0)

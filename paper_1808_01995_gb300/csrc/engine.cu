@@ -566,6 +566,18 @@ struct Prop {
   uint2 *tb_bits = nullptr;  // [tile][nzw] damping words of the two-step tiles
 };
 
+// dt, dt^2 and dt/2 for the coefficient kernel, each as a float pair hi + lo
+static void coef_set_dt(CoefArgs *a, double dt) {
+  auto split = [](double v, float *hi, float *lo) {
+    *hi = static_cast<float>(v);
+    *lo = static_cast<float>(v - static_cast<double>(*hi));
+  };
+  a->dt = dt;
+  split(dt, &a->dt_hi, &a->dt_lo);
+  split(dt * dt, &a->dt2_hi, &a->dt2_lo);
+  split(0.5 * dt, &a->hdt_hi, &a->hdt_lo);
+}
+
 static int prop_setup(wp_ctx *c, Arena &ar, const Geom &G, const float *m, const float *eta, Prop *P) {
   P->c = c;
   P->G = G;
@@ -579,7 +591,7 @@ static int prop_setup(wp_ctx *c, Arena &ar, const Geom &G, const float *m, const
   a.m = m;
   a.eta = eta;
   a.g = G.fg();
-  a.dt = G.dt;
+  coef_set_dt(&a, G.dt);
   a.b = P->b.p;
   a.s = P->s.p;
   if (G.ndim == 3) {
@@ -2272,7 +2284,7 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
   ca.m = m;
   ca.eta = eta;
   ca.g = G.fg();
-  ca.dt = G.dt;
+  coef_set_dt(&ca, G.dt);
   ca.b = b;
   ca.s = s;
   ca.tflag = tflag;

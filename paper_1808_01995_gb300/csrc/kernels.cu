@@ -85,25 +85,73 @@ cudaError_t launch_stencil2d(int R, int mode, cudaStream_t st, const Stencil2dAr
 // flags (bytes, then packed into per-tile z bitmasks by a second kernel);
 // max(1/m) for the CFL check; non-finite / sign checks of the inputs.
 // ---------------------------------------------------------------------------
+// Double-float arithmetic (a value as an unevaluated sum hi + lo of two floats),
+// from the error-free transformations of Dekker (product, with an FMA) and Knuth
+// (sum): about 44 significant bits in FP32 instructions, where this GPU's FP64
+// rate would make a per-point FP64 division the kernel's bottleneck.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return DF{p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return DF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF df_norm(float hi, float lo) {  // |lo| small against hi
+  const float s = __fadd_rn(hi, lo);
+  return DF{s, __fsub_rn(lo, __fsub_rn(s, hi))};
+}
+// a (double-float) times a float
+__device__ __forceinline__ DF df_mul_f(DF a, float b) {
+  DF p = df_two_prod(a.hi, b);
+  return df_norm(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+// n / d rounded once to float: the float quotient q1 plus a correction from the
+// exact remainder n - q1 d (Dekker's division step)
+__device__ __forceinline__ float df_div_to_float(DF n, DF d) {
+  const float q1 = __fdiv_rn(n.hi, d.hi);
+  const DF t = df_two_prod(q1, d.hi);
+  float r = __fsub_rn(n.hi, t.hi);  // exact: t.hi is within a factor 2 of n.hi
+  r = __fsub_rn(r, t.lo);
+  r = __fadd_rn(r, n.lo);
+  r = __fmaf_rn(-q1, d.lo, r);
+  return __fadd_rn(q1, __fdiv_rn(r, d.hi));
+}
+
+// A1: b = dt^2 / D, s = -eta dt / D, D = m + eta dt/2 (double-float, rounded once to
+// float), damping flags per (plane, flag tile), input checks and max(1/m).  One
+// grid row (z, y) per block iteration: no 64-bit index division per point.
 __global__ void coef_kernel(const CoefArgs a) {
-  const long long nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-  const long long n = nx * ny * nz;
+  const int nx = a.g.nx, ny = a.g.ny;
+  const long long nrows = static_cast<long long>(ny) * a.g.nz;
+  const DF dt = {a.dt_hi, a.dt_lo};
+  const DF dt2 = {a.dt2_hi, a.dt2_lo};
+  const DF hdt = {a.hdt_hi, a.hdt_lo};
   float local_max = 0.f;
   int bad = 0;
-  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const float mf = a.m[i], ef = a.eta[i];
-    if (!isfinite(mf) || !isfinite(ef)) bad |= 1;
-    if (!(mf > 0.f) || !(ef >= 0.f)) bad |= 2;
-    const long long x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
-    const double m = mf, e = ef;
-    const double D = m + e * a.dt * 0.5;
-    const long long gi = z * a.g.plane + y * a.g.pitch + x;
-    a.b[gi] = static_cast<float>(a.dt * a.dt / D);
-    a.s[gi] = static_cast<float>(-e * a.dt / D);
-    if (a.tflag && ef != 0.f)
-      a.tflag[(z * a.tiles_y + y / a.tile_h) * a.tiles_x + x / a.tile_w] = 1;
-    if (mf > 0.f) local_max = fmaxf(local_max, 1.0f / mf);
+  for (long long row = blockIdx.x; row < nrows; row += gridDim.x) {
+    const int y = static_cast<int>(row % ny);
+    const long long z = row / ny;
+    const long long ci = row * nx;                       // contiguous input row
+    const long long gi = z * a.g.plane + static_cast<long long>(y) * a.g.pitch;  // pitched row
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+      const float mf = a.m[ci + x], ef = a.eta[ci + x];
+      if (!isfinite(mf) || !isfinite(ef)) bad |= 1;
+      if (!(mf > 0.f) || !(ef >= 0.f)) bad |= 2;
+      // D = m + eta (dt/2)
+      const DF eh = df_mul_f(hdt, ef);
+      const DF s0 = df_two_sum(mf, eh.hi);
+      const DF D = df_norm(s0.hi, __fadd_rn(s0.lo, eh.lo));
+      a.b[gi + x] = df_div_to_float(dt2, D);
+      a.s[gi + x] = ef != 0.f ? -df_div_to_float(df_mul_f(dt, ef), D) : -0.f;
+      if (a.tflag && ef != 0.f)
+        a.tflag[(z * a.tiles_y + y / a.tile_h) * a.tiles_x + x / a.tile_w] = 1;
+      if (mf > 0.f) local_max = fmaxf(local_max, __frcp_rn(mf));
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -136,8 +184,8 @@ __global__ void pack_flags_kernel(const CoefArgs a) {
 }
 
 cudaError_t launch_coef(cudaStream_t st, const CoefArgs &a) {
-  const long long n = static_cast<long long>(a.g.nx) * a.g.ny * a.g.nz;
-  long long blocks = (n + 255) / 256;
+  const long long nrows = static_cast<long long>(a.g.ny) * a.g.nz;
+  long long blocks = nrows;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
   coef_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(a);

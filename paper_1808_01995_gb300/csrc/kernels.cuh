@@ -79,6 +79,7 @@ struct CoefArgs {
   const float *eta;
   FieldGeom g;
   double dt;
+  float dt_hi, dt_lo, dt2_hi, dt2_lo, hdt_hi, hdt_lo;  // dt, dt^2, dt/2 as float pairs (hi + lo)
   float *b;                // pitched
   float *s;                // pitched
   unsigned char *tflag;    // 3D only: [nz][tiles_y][tiles_x] bytes, 1 where eta != 0, pre-zeroed
