@@ -36,6 +36,9 @@ namespace wp {
 #ifndef WP_TB_NY
 #define WP_TB_NY 4       // rows per lane, R > 2 (one CTA per SM)
 #endif
+#ifndef WP_TB_WARPS
+#define WP_TB_WARPS 8    // warps per CTA (each lane: two x points in NY rows)
+#endif
 #ifndef WP_TB_ZU
 #define WP_TB_ZU 1       // planes per unrolled z step (1 or 2; 1 measured faster: smaller code)
 #endif
@@ -50,9 +53,10 @@ struct CfgTb {
   static_assert(R >= 1 && R <= 4, "the two-step kernel covers space orders 2..8");
   static constexpr int NX = 2;
   static constexpr int NY = R <= 2 ? WP_TB_NY_LO : WP_TB_NY;
-  static constexpr int MINB = NY <= 2 ? 2 : 1;     // CTAs per SM the registers must allow
+  static constexpr int MINB = NY <= 2 && WP_TB_WARPS <= 8 ? 2 : 1;  // CTAs per SM the registers must allow
   static constexpr int W = 32 * NX;                // region width (step 1)
-  static constexpr int H = kConsumerWarps * NY;    // region height
+  static constexpr int WARPS = WP_TB_WARPS;
+  static constexpr int H = WARPS * NY;             // region height
   static constexpr int RX = 4;                     // x rim, 16 bytes for TMA
   static constexpr int RE = (R + 1) / 2 * 2;       // x window half-width (even)
   static constexpr int CW = W - 2 * RX;            // core width (step 2)
@@ -103,7 +107,7 @@ struct Stencil3dTbArgs {
   const float *b;               // pitched b (the injection weight)
 };
 
-constexpr int kThreadsTb = kConsumerWarps * 32;
+constexpr int kThreadsTb = WP_TB_WARPS * 32;
 
 // tm: [0] u^n (plane box UPW x UPH), [1] u^{n-1}, [2] b, [3] s (region boxes W x H),
 //     [4] b, [5] s (core boxes CW x CH)
@@ -144,15 +148,15 @@ __global__ void __launch_bounds__(kThreadsTb, CfgTb<R>::MINB)
   if (tid == 0) {
     for (int i = 0; i < C::NSU; ++i) {
       mbar_init(&full_u[i], 1);
-      mbar_init(&empty_u[i], kConsumerWarps);
+      mbar_init(&empty_u[i], C::WARPS);
     }
     for (int i = 0; i < C::NST; ++i) {
       mbar_init(&full_t[i], 1);
-      mbar_init(&empty_t[i], kConsumerWarps);
+      mbar_init(&empty_t[i], C::WARPS);
     }
     for (int i = 0; i < C::NSC; ++i) {
       mbar_init(&full_c[i], 1);
-      mbar_init(&empty_c[i], kConsumerWarps);
+      mbar_init(&empty_c[i], C::WARPS);
     }
     *abort_flag = 0;
     mbar_init_fence();
@@ -309,7 +313,7 @@ __global__ void __launch_bounds__(kThreadsTb, CfgTb<R>::MINB)
     __syncwarp();
     if (lane == 0) mbar_arrive(bar);
   };
-  auto cbar = [&]() { asm volatile("bar.sync 1, %0;" ::"n"(kConsumerWarps * 32) : "memory"); };
+  auto cbar = [&]() { asm volatile("bar.sync 1, %0;" ::"n"(C::WARPS * 32) : "memory"); };
   const long long drow = a.ntarget ? a.row + (a.row_base ? *a.row_base : 0) : 0;
 
   for (int it = 0, item = first_item(0); item < item_end; item = first_item(++it)) {
