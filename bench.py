@@ -60,6 +60,8 @@ def parse():
                    help="timed FWI gradients of the 200^3 + 40 blobs workload (0 skips the gradient leg)")
     p.add_argument("--gradient-nt", type=int, default=1500,
                    help="time steps of the gradient workload (1500; fewer only for profiling)")
+    p.add_argument("--large-nt", type=int, default=3000,
+                   help="time steps of the full-size SO16 salt leg (0 skips it)")
     p.add_argument("--checkpoints", type=int, default=20,
                    help="stored states of the binomial-checkpointing gradient timed beside it (0 skips it)")
     p.add_argument("--no-full-history", dest="full_history", action="store_false",
@@ -422,6 +424,55 @@ def gradient_leg(args):
             "full_history": fh, "binomial_checkpointing": ck, "boundary_reconstruction": rc}
 
 
+def large_leg(args):
+    """The SO16 salt workload at full size: 512 x 512 x 400 interior + 40-point layer
+    (592 x 592 x 480, 168 M points), 3000 steps, 256 x 256 receivers: one forward
+    shot and one FWI gradient with snapshots every 20 steps (about 220 GB)."""
+    import torch
+    from paper_1808_01995_gb300 import synth
+    from paper_1808_01995_gb300 import wavprop as W
+    torch.cuda.empty_cache()
+    true = synth.salt_3d()
+    k, nt, S = 16, args.large_nt, 20
+    dt = 0.9 * W.wp_cfl_dt(W.Grid(true.shape, true.spacing, true.origin, k), true.vmax)
+    grid = W.Grid(true.shape, true.spacing, true.origin, k, dt, nt)
+    need = W.wp_estimate_bytes(grid, 1, len(true.rec), 1, S)
+    free, _ = torch.cuda.mem_get_info()
+    desc = f"salt3d 512x512x400 + 40 ({'x'.join(map(str, true.shape))}) SO16, nt={nt}, {len(true.rec)} receivers"
+    if need > 0.85 * free:
+        return {"workload": desc, "skipped": f"needs {need / 2**30:.0f} GiB, {free / 2**30:.0f} GiB free"}
+    ctx = W.Context(0)
+    m = torch.from_numpy(true.m32()).cuda()
+    eta = torch.from_numpy(true.eta32()).cuda()
+    q = torch.from_numpy(true.wavelet(dt, nt)).cuda()
+    d = torch.zeros((nt, len(true.rec)), device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    W.wp_forward_dev(ctx.handle, grid, m, eta, q, true.src, true.rec, d)
+    torch.cuda.synchronize()
+    e0.record()
+    W.wp_forward_dev(ctx.handle, grid, m, eta, q, true.src, true.rec, d)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1)
+    g = torch.empty_like(m)
+    d_obs = torch.zeros_like(d)
+    W.wp_fwi_gradient_dev(ctx.handle, grid, m, eta, q, true.src, d_obs, true.rec, S, g)
+    torch.cuda.synchronize()
+    e0.record()
+    J = W.wp_fwi_gradient_dev(ctx.handle, grid, m, eta, q, true.src, d_obs, true.rec, S, g)
+    e1.record()
+    torch.cuda.synchronize()
+    grad_ms = e0.elapsed_time(e1)
+    npts = int(np.prod(true.shape))
+    out = {"workload": desc, "forward_ms": fwd_ms, "forward_gpts_per_s": npts * nt / (fwd_ms * 1e-3) / 1e9,
+           "gradient_ms": grad_ms, "gradient_snap_interval": S, "misfit": J,
+           "device_bytes": int(W.wp_bytes_in_use(ctx.handle))}
+    ctx.close()
+    del m, eta, q, d, g, d_obs
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     world, rank, local = dist_init()
     import torch
@@ -525,6 +576,10 @@ def run_ours(args):
     if args.serving > 0 and world == 1:
         serving = serving_leg(args)
 
+    large = None
+    if args.large_nt > 0 and world == 1:
+        large = large_leg(args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, steps, el, nthreads = oracle_sample(model, dt, args.cpu_seconds)
@@ -536,7 +591,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": describe(model, nt, dt),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clk.summary(), "gradient": gradient, "serving": serving}
+                "clocks": clk.summary(), "gradient": gradient, "serving": serving, "large": large}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
