@@ -513,18 +513,19 @@ struct Plan3d {
 };
 
 // tx x ty tiles; every item streams its chunk plus `extra` planes
-static Plan3d plan_items(const Geom &G, int tx, int ty, int extra, int num_sms, int occ) {
+// tx x ty tiles over an nx x ny x nz box; every item streams its chunk plus `extra` planes
+static Plan3d plan_items(int nx, int ny, int nz, int R, int tx, int ty, int extra, int num_sms, int occ) {
   Plan3d p;
-  p.tiles_x = (G.nx + tx - 1) / tx;
-  p.tiles_y = (G.ny + ty - 1) / ty;
+  p.tiles_x = (nx + tx - 1) / tx;
+  p.tiles_y = (ny + ty - 1) / ty;
   const long long tiles = static_cast<long long>(p.tiles_x) * p.tiles_y;
   const long long ctas = static_cast<long long>(num_sms) * std::max(occ, 1);
   double best = 1e300;
-  const int min_chunk = std::min(G.nz, std::max(2 * G.R, 8));
-  for (int nzc = 1; nzc <= G.nz; ++nzc) {
-    const int zc = (G.nz + nzc - 1) / nzc;
+  const int min_chunk = std::min(nz, std::max(2 * R, 8));
+  for (int nzc = 1; nzc <= nz; ++nzc) {
+    const int zc = (nz + nzc - 1) / nzc;
     if (zc < min_chunk) break;
-    const int n_eff = (G.nz + zc - 1) / zc;
+    const int n_eff = (nz + zc - 1) / zc;
     const long long items = tiles * n_eff;
     const long long rounds = (items + ctas - 1) / ctas;
     const double used = std::min(1.0, double(items) / double(ctas));
@@ -538,12 +539,15 @@ static Plan3d plan_items(const Geom &G, int tx, int ty, int extra, int num_sms, 
   }
   const char *env = getenv("WP_ZCHUNK");
   if (env && atoi(env) > 0) {
-    p.zchunk = std::min(G.nz, atoi(env));
-    p.nzc = (G.nz + p.zchunk - 1) / p.zchunk;
+    p.zchunk = std::min(nz, atoi(env));
+    p.nzc = (nz + p.zchunk - 1) / p.zchunk;
   }
   p.nitems = int(tiles * p.nzc);
   p.grid = dim3(unsigned(std::min<long long>(p.nitems, ctas)));
   return p;
+}
+static Plan3d plan_items(const Geom &G, int tx, int ty, int extra, int num_sms, int occ) {
+  return plan_items(G.nx, G.ny, G.nz, G.R, tx, ty, extra, num_sms, occ);
 }
 
 static Plan3d plan3d(const Geom &G, int mode, int num_sms, int occ) {
@@ -561,6 +565,9 @@ struct Prop {
   Field3 b, s;
   unsigned *tbits = nullptr;
   Plan3d plan[2];
+  bool sub = false;  // a sub-box for prop_step(..., sub = true): box (x0 a multiple of 4) and its plans
+  Box box;
+  Plan3d plan_sub[2];
   bool tb = false;  // the two-step kernel covers this grid
   Plan3d plan_tb;
   uint2 *tb_bits = nullptr;  // [tile][nzw] damping words of the two-step tiles
@@ -726,7 +733,7 @@ static int wait_event(wp_ctx *c, cudaEvent_t ev, const char *what) {
 }
 
 static int prop_step(Prop &P, const Field3 &u, const Field3 &um, float *out, int mode, const Field3 *uj,
-                     const Field3 *grad) {
+                     const Field3 *grad, bool sub = false) {
   const Geom &G = P.G;
   P.c->prof_open = P.c->profiling && (P.c->prof_seq++ % uint64_t(P.c->prof_every)) == 0;
   if (P.c->prof_open) TRY(prof_mark(P.c));
@@ -734,9 +741,22 @@ static int prop_step(Prop &P, const Field3 &u, const Field3 &um, float *out, int
     // never hand the kernel a descriptor that was not encoded for its buffer
     if (!u.mapped || !um.mapped || !P.b.mapped || !P.s.mapped || (uj && !uj->mapped) || (grad && !grad->mapped))
       return fail(WP_ECUDA, "internal error: a field of the 3D stencil has no TMA descriptor");
-    const Plan3d &pl = P.plan[mode];
+    const bool in_box = sub && P.sub;
+    const Plan3d &pl = in_box ? P.plan_sub[mode] : P.plan[mode];
     Stencil3dArgs a;
     memset(&a, 0, sizeof a);
+    if (in_box) {
+      a.bx0 = P.box.x0;
+      a.by0 = P.box.y0;
+      a.bz0 = P.box.z0;
+      a.bx1 = P.box.x1;
+      a.by1 = P.box.y1;
+      a.bz1 = P.box.z1;
+    } else {
+      a.bx1 = G.nx;
+      a.by1 = G.ny;
+      a.bz1 = G.nz;
+    }
     a.g = G.fg();
     a.c = P.lc;
     a.u = u.p;
@@ -1936,6 +1956,14 @@ static int gradient_recon_impl(wp_ctx *c, const wp_grid *grid, const float *m, c
   Box Z;
   TRY(undamped_box(c, G, S.eta_d, &Z));
   const RingBoxes rb = ring_boxes(G, Z);
+  if (G.ndim == 3) {  // the backward update runs on Z only (x start rounded down for TMA)
+    S.P.sub = true;
+    S.P.box = Z;
+    S.P.box.x0 = Z.x0 & ~3;
+    const Box &bx = S.P.box;
+    S.P.plan_sub[0] = plan_items(bx.x1 - bx.x0, bx.y1 - bx.y0, bx.z1 - bx.z0, G.R, stencil3d_tile_x(G.R, 0),
+                                 stencil3d_tile_y(G.R, 0), G.R, c->num_sms, c->occ3d[0][G.R]);
+  }
   const long long nring = rb.start[rb.n];
   const int nstore = std::max(G.nt - 2, 0);  // levels 1 .. nt-2
   float *store = nullptr;
@@ -1967,7 +1995,7 @@ static int gradient_recon_impl(wp_ctx *c, const wp_grid *grid, const float *m, c
     TRY(prop_inject(S.P, S.drec, S.r_d, j - 1, w2.p, g.p, hi->p));
     if (j >= 3) {
       // u^{j-2} = u^{j-1} + (u^{j-1} - u^j) + b L u^{j-1} + b P_s^T q^{j-1} on Z, into hi
-      TRY(prop_step(S.P, *lo, *hi, hi->p, kModeFwd, nullptr, nullptr));
+      TRY(prop_step(S.P, *lo, *hi, hi->p, kModeFwd, nullptr, nullptr, true));
       TRY(prop_inject(S.P, S.dsrc, S.q_d, j - 1, hi->p, nullptr, nullptr));
       if (nring) {
         CU(launch_ring_copy(c->stream, hi->p, G.fg(), store + size_t(j - 3) * nring, rb, false));

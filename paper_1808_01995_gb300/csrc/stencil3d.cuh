@@ -106,6 +106,9 @@ struct Stencil3dArgs {
   int zchunk, nzc;              // planes per item, chunks per column
   int nitems;                   // tiles_x * tiles_y * nzc
   int *err;
+  // updated box [bx0, bx1) x [by0, by1) x [bz0, bz1) (the whole grid normally; bx0 a
+  // multiple of 4); neighbours outside it are read, only points inside are written
+  int bx0, by0, bz0, bx1, by1, bz1;
 };
 
 // ---- scalar / packed-pair arithmetic -------------------------------------
@@ -171,8 +174,8 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
     const int tile = item / a.nzc, zc = item - tile * a.nzc;
     tx = tile % a.tiles_x;
     ty = tile / a.tiles_x;
-    z0 = zc * a.zchunk;
-    z1 = min(z0 + a.zchunk, a.g.nz);
+    z0 = a.bz0 + zc * a.zchunk;
+    z1 = min(z0 + a.zchunk, a.bz1);
   };
 
   if (warp == kConsumerWarps) {
@@ -233,7 +236,7 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
         int tx, ty, z0, z1;
         item_geom(item, tx, ty, z0, z1);
         if (z0 >= z1) continue;
-        const int x0 = tx * TX, y0 = ty * TY;
+        const int x0 = a.bx0 + tx * TX, y0 = a.by0 + ty * TY;
         // damping bits of the flag tiles covered by this work tile
         const int fx0 = x0 / kFlagTX, fx1 = min((x0 + TX - 1) / kFlagTX + 1, a.flag_tiles_x);
         const int fy0 = y0 / kTileFlagTY, fy1 = min((y0 + TY - 1) / kTileFlagTY + 1, a.flag_tiles_y);
@@ -286,16 +289,16 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
     int tx, ty, z0, z1;
     item_geom(item, tx, ty, z0, z1);
     if (z0 >= z1) continue;
-    const int gx = tx * TX + NX * lane;
-    const int y0 = ty * TY;
-    const bool xin0 = gx < a.g.nx;
-    const bool xin1 = NX == 2 && gx + 1 < a.g.nx;
+    const int gx = a.bx0 + tx * TX + NX * lane;
+    const int y0 = a.by0 + ty * TY;
+    const bool xin0 = gx < a.bx1;
+    const bool xin1 = NX == 2 && gx + 1 < a.bx1;
     bool yin[NY];
     long long rbase[NY];  // in-plane offset of each row (row clamped inside the grid)
 #pragma unroll
     for (int r = 0; r < NY; ++r) {
       const int gy = y0 + ty0 + r;
-      yin[r] = gy < a.g.ny;
+      yin[r] = gy < a.by1;
       rbase[r] = static_cast<long long>(min(gy, a.g.ny - 1)) * a.g.pitch;
     }
     const int gxc0 = min(gx, a.g.nx - 1), gxc1 = min(gx + 1, a.g.nx - 1);
