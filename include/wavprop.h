@@ -129,7 +129,10 @@ int wp_adjoint(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *et
  * snapshot pairs every snap_interval steps in device memory and recomputed
  * between them (Sec. 3.3, checkpointing); snap_interval = 1 keeps the whole
  * history instead (each level stored once, nt fields, written by the forward
- * step itself) and recomputes nothing.  grad_out has the field's shape. */
+ * step itself) and recomputes nothing; snap_interval = 0 chooses: the whole
+ * history if it fits the context's remaining budget, else the smallest interval
+ * that fits (WP_ENOMEM if none does).  The gradient is the same whichever
+ * interval is used.  grad_out has the field's shape. */
 int wp_gradient(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *eta,
                 const float *wavelet, int nsrc, const double *src_coords,
                 const float *residual, int nrec, const double *rec_coords, int snap_interval,

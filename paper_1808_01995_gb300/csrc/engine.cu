@@ -1267,7 +1267,23 @@ static int forward_save(wp_ctx *c, const wp_grid *grid, const float *m, const fl
     if (nsrc < 0 || nrec < 0) return fail(WP_EINVAL, "point counts must be >= 0");
     if (!m || !eta) return fail(WP_EINVAL, "m and eta must not be NULL");
     if (nsrc > 0 && G.nt > 0 && !wavelet) return fail(WP_EINVAL, "wavelet is NULL");
-    if (snap_interval < 1) return fail(WP_EINVAL, "snap_interval must be >= 1");
+    if (snap_interval < 0) return fail(WP_EINVAL, "snap_interval must be >= 0");
+    if (snap_interval == 0) {
+      // automatic: the whole history if it fits the budget left, else the smallest
+      // snapshot interval that fits (fields: state + snapshots + recompute ring +
+      // adjoint and gradient, with 5 % headroom)
+      const double f = double(round_up(G.field_bytes(), 256));
+      const double avail = 0.95 * (double(c->budget) - double(c->in_use)) - 8.0 * f;
+      auto need = [&](int S) -> double {
+        if (S == 1) return (double(G.nt) + 5.0) * f;
+        const double nseg = std::ceil(double(G.nt) / S);
+        return (2.0 * nseg + std::min(S, std::max(G.nt, 1)) + 5.0) * f;
+      };
+      int S = 1;
+      while (S <= std::max(G.nt, 1) && need(S) > avail) S = S == 1 ? 2 : S + std::max(1, S / 4);
+      if (S > std::max(G.nt, 1)) return fail(WP_ENOMEM, "no snapshot interval fits the device budget");
+      snap_interval = S;
+    }
     st->S = snap_interval;
     st->nseg = (G.nt + st->S - 1) / st->S;
     TRY(build_points(G, nsrc, src_xyz, &st->psrc, "source"));

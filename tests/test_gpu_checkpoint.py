@@ -132,3 +132,27 @@ def test_full_history_autograd_and_receivers(ctx):
         misfit(d, torch.zeros_like(d)).backward()
         grads.append(m.grad.cpu().numpy())
     assert np.array_equal(grads[0], grads[1])
+
+
+def test_automatic_snapshot_interval(ctx):
+    """snap_interval = 0: the whole history when it fits, else the smallest interval
+    that fits the context's budget; the gradient is the same either way."""
+    true, og, wg, q, r = case((24, 26, 28), 4, 60, 47)
+    m, e = true.m32(), true.eta32()
+    g1 = W.wp_gradient(ctx.handle, wg, m, e, q, true.src, r, true.rec, 1)
+    g_auto = W.wp_gradient(ctx.handle, wg, m, e, q, true.src, r, true.rec, 0)
+    assert np.array_equal(g_auto, g1)
+    field = 24 * 26 * 32 * 4  # pitched field bytes (x padded to 32)
+    small = W.Context(0, hbm_budget_bytes=50 * field)
+    try:
+        g_tight = W.wp_gradient(small.handle, wg, m, e, q, true.src, r, true.rec, 0)
+        assert W.wp_bytes_in_use(small.handle) <= 50 * field
+    finally:
+        small.close()
+    assert np.array_equal(g_tight, g1)
+    tiny = W.Context(0, hbm_budget_bytes=12 * field)
+    try:
+        with pytest.raises(W.WpError):
+            W.wp_gradient(tiny.handle, wg, m, e, q, true.src, r, true.rec, 0)
+    finally:
+        tiny.close()

@@ -63,7 +63,9 @@ def case(shape, k, nt, seed, nbl=6):
 
 
 @pytest.mark.parametrize("shape,k,nt", [((30, 33, 37), 8, 80), ((34, 29, 31), 16, 60), ((61, 57), 4, 200),
-                                        ((40, 45), 2, 150)])
+                                        ((40, 45), 2, 150),
+                                        ((27, 31, 35), 2, 90),    # box x start rounded beyond the 1-point ring
+                                        ((29, 26, 41), 6, 70)])
 def test_reconstructed_gradient_matches_oracle_on_the_undamped_box(ctx, shape, k, nt):
     true, og, wg, q, r = case(shape, k, nt, 11)
     m, e = true.m32(), true.eta32()
