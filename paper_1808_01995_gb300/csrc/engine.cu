@@ -2396,6 +2396,9 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
       a.nzc = pl.nzc;
       a.nitems = pl.nitems;
       a.err = scal;
+      a.bx1 = G.nx;  // the whole grid
+      a.by1 = G.ny;
+      a.bz1 = G.nz;
       const CUtensorMap maps[6] = {halo[k & 1], tile[(k + 1) & 1], tb, ts, tb, tb};
       CU(launch_stencil3d_fwd(G.R, pl.grid, st, maps, a));
     } else {
