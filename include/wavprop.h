@@ -247,15 +247,16 @@ int wp_forward_save(wp_ctx *ctx, const wp_grid *grid, const float *m, const floa
 int wp_backward(wp_state *state, const float *residual, float *grad_out, void *stream);
 void wp_state_free(wp_state *state);
 
-/* With enable != 0, forward (and few-receiver adjoint) time loops of 3D grids
- * with space order <= 8 and at most 64 injection targets take two time steps
- * per stencil launch (temporal blocking: u^{n+1} stays on chip for the second
- * step, two extra wavefields); results are identical either way.  Default off
- * (on if WP_TEMPORAL_BLOCKING=1 is set when the context is created): on GB300
- * the two-step kernel is slower than two single steps (it is latency-bound at
- * one CTA per SM).  No counterpart in the paper, which blocks loops in space
- * only. */
-int wp_set_temporal_blocking(wp_ctx *ctx, int enable);
+/* Temporal blocking of forward (and few-receiver adjoint) time loops of 3D grids
+ * with space order <= 8 and at most 64 injection targets; results are identical
+ * in every mode.  mode 0: one stencil launch per time step (default); 1: two
+ * steps per launch, u^{n+1} kept on chip with the rim computed twice; 2: two steps
+ * per launch by two roles of CTAs (one cooperative launch, one grid column per
+ * CTA; u^{n+1} read back from L2), used when twice the columns fit on the GPU at
+ * once.  Both need two extra wavefields.  The initial mode comes from
+ * WP_TEMPORAL_BLOCKING when the context is created.  No counterpart in the paper,
+ * which blocks loops in space only. */
+int wp_set_temporal_blocking(wp_ctx *ctx, int mode);
 
 /* Device bytes currently held by the context (including live states). */
 size_t wp_bytes_in_use(const wp_ctx *ctx);

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libwavprop.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["engine.cu", "kernels.cu", "stencil3d_fwd.cu", "stencil3d_adj.cu", "stencil3d_tb.cu"]
+SOURCES = ["engine.cu", "kernels.cu", "stencil3d_fwd.cu", "stencil3d_adj.cu", "stencil3d_tb.cu", "stencil3d_pair.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

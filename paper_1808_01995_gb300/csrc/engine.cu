@@ -73,7 +73,8 @@ struct wp_ctx {
   int occ3d[2][9] = {};
   int ty3d[2][9] = {};
   int smem_tb[5] = {}, occ_tb[5] = {};     // two-step kernel, half-orders 1..4
-  bool temporal_blocking = false;         // forward loops take two steps per stencil launch
+  int smem_pair[5] = {}, occ_pair[5] = {}; // two-role (pair) kernel, half-orders 1..4
+  int temporal_blocking = 0;              // 0 single steps; 1 two-step kernel; 2 CTA pairs
   bool broken = false;
   // profiling: an event pair around every prof_every-th stencil launch, summed on read
   bool profiling = false;
@@ -570,6 +571,9 @@ struct Prop {
   Plan3d plan_sub[2];
   bool tb = false;  // the two-step kernel covers this grid
   Plan3d plan_tb;
+  bool pair = false;  // the two-role kernel covers this grid: one column per CTA, all resident
+  Plan3d plan_pair;
+  unsigned *progress = nullptr;  // [column] planes of u^{n+1} published
   uint2 *tb_bits = nullptr;  // [tile][nzw] damping words of the two-step tiles
 };
 
@@ -633,6 +637,17 @@ static int prop_setup(wp_ctx *c, Arena &ar, const Geom &G, const float *m, const
     TRY(make_field_maps(&P->b, G));
     TRY(make_field_maps(&P->s, G));
     for (int mode = 0; mode < 2; ++mode) P->plan[mode] = plan3d(G, mode, c->num_sms, c->occ3d[mode][G.R]);
+    if (G.R <= 4 && c->occ_pair[G.R] > 0) {
+      // the single-step plan's items; half the resident CTAs per role
+      Plan3d pp = plan3d(G, kModeFwd, c->num_sms, std::max(1, c->occ_pair[G.R] / 2));
+      const long long per_role = static_cast<long long>(c->occ_pair[G.R]) * c->num_sms / 2;
+      pp.grid = dim3(unsigned(2 * std::min<long long>(pp.nitems, per_role)));
+      if (per_role >= 1) {
+        P->pair = true;
+        P->plan_pair = pp;
+        TRY(ar.alloc(&P->progress, size_t(pp.nitems)));
+      }
+    }
     TbShape sh;
     if (stencil3d_tb_shape(G.R, &sh) && c->occ_tb[G.R] > 0) {
       P->tb = true;
@@ -869,6 +884,69 @@ static int prop_step2(Prop &P, const Field3 &um, const Field3 &u, Field3 &out1, 
   return WP_OK;
 }
 
+// Two forward steps by the two-role kernel: (u^{n-1}, u^n) = (um, u) -> (out1, out2)
+// with data row `row` (+ *row_base) injected into u^{n+1}; the caller injects the
+// next row into out2.
+static int prop_pair(Prop &P, const Field3 &um, const Field3 &u, Field3 &out1, Field3 &out2, const DevPoints &inj,
+                     const float *data, long long row, const long long *row_base) {
+  const Geom &G = P.G;
+  if (!P.pair || !um.mapped || !u.mapped || !out1.mapped || !P.b.mapped || !P.s.mapped)
+    return fail(WP_ECUDA, "internal error: the pair stencil cannot run on this grid");
+  if (inj.ntarget > kPairMaxTargets) return fail(WP_ECUDA, "internal error: too many targets for the pair stencil");
+  P.c->prof_open = P.c->profiling && (P.c->prof_seq++ % uint64_t(P.c->prof_every)) == 0;
+  const Plan3d &pl = P.plan_pair;
+  Stencil3dArgs a;
+  memset(&a, 0, sizeof a);
+  a.g = G.fg();
+  a.c = P.lc;
+  a.u = u.p;
+  a.out = out1.p;
+  a.grad = out2.p;
+  a.tbits = P.tbits;
+  a.nzw = G.nzw;
+  a.tiles_x = pl.tiles_x;
+  a.tiles_y = pl.tiles_y;
+  a.flag_tiles_x = G.tiles_x;
+  a.flag_tiles_y = G.tiles_y;
+  a.zchunk = pl.zchunk;
+  a.nzc = pl.nzc;
+  a.nitems = pl.nitems;
+  a.err = P.c->d_scalars;
+  a.bx1 = G.nx;
+  a.by1 = G.ny;
+  a.bz1 = G.nz;
+  a.progress = P.progress;
+  a.ntarget = data ? inj.ntarget : 0;
+  a.target = inj.target;
+  a.rowptr = inj.rowptr;
+  a.pid = inj.pid;
+  a.w = inj.cw;
+  a.data = data;
+  a.npts = inj.npts;
+  a.row_base = row_base;
+  a.row = row;
+  a.b = P.b.p;
+  const CUtensorMap maps[6] = {u.halo[0], um.tile[0], P.b.tile[0], P.s.tile[0], out1.halo[0], u.tile[0]};
+  if (P.c->hashing) {
+    hash_bytes(P.c, &a, sizeof a);
+    hash_bytes(P.c, maps, sizeof maps);
+    hash_bytes(P.c, &pl.grid, sizeof pl.grid);
+    if (P.c->prof_open) TRY(prof_mark(P.c));
+    return P.c->prof_open ? prof_mark(P.c) : WP_OK;
+  }
+  CU(cudaMemsetAsync(P.progress, 0, size_t(pl.nitems) * sizeof(unsigned), P.c->stream));
+  if (P.c->prof_open) TRY(prof_mark(P.c));
+  cudaError_t e = launch_stencil3d_pair(G.R, pl.grid, P.c->stream, maps, a);
+  if (e != cudaSuccess) return fail(WP_ECUDA, "pair stencil launch failed: %s", cudaGetErrorString(e));
+  P.c->launches++;
+  if (P.c->prof_open) TRY(prof_mark(P.c));
+  if (!P.c->capturing && P.c->prof_used >= 4096) {
+    TRY(ctx_wait(P.c));
+    TRY(prof_collect(P.c));
+  }
+  return WP_OK;
+}
+
 static int prop_inject(Prop &P, const DevPoints &dp, const float *data, long long row, float *u, float *grad,
                        const float *uj, const long long *row_base = nullptr) {
   if (dp.ntarget == 0) return WP_OK;
@@ -1068,7 +1146,10 @@ static int run_loop(Prop &P, Field3 u[2], int nt, const DevPoints &inj, const fl
 // Whether the time loop can take two steps per launch (3D, the two-step kernel
 // covers the order, few enough injection targets, switched on).
 static bool two_step_ok(const Prop &P, const DevPoints &inj, int nt) {
-  return P.G.ndim == 3 && P.tb && P.c->temporal_blocking && inj.ntarget <= kTbMaxTargets && nt >= 2;
+  if (P.G.ndim != 3 || nt < 2) return false;
+  if (P.c->temporal_blocking == 1) return P.tb && inj.ntarget <= kTbMaxTargets;
+  if (P.c->temporal_blocking == 2) return P.pair && inj.ntarget <= kPairMaxTargets;
+  return false;
 }
 
 // The same time loop two steps per stencil launch, over four fields: the pair
@@ -1082,7 +1163,10 @@ static int run_loop2(Prop &P, Field3 u[4], int nt, const DevPoints &inj, const f
   auto pair = [&](int j, long long ra, long long rb_, const long long *base) -> int {
     Field3 &um = u[(j & 1) ? 2 : 0], &uc = u[(j & 1) ? 3 : 1];
     Field3 &o1 = u[(j & 1) ? 0 : 2], &o2 = u[(j & 1) ? 1 : 3];
-    TRY(prop_step2(P, um, uc, o1, o2, inj, data, ra, base));
+    if (c->temporal_blocking == 2)
+      TRY(prop_pair(P, um, uc, o1, o2, inj, data, ra, base));
+    else
+      TRY(prop_step2(P, um, uc, o1, o2, inj, data, ra, base));
     TRY(prop_inject(P, inj, data, rb_, o2.p, nullptr, nullptr, base));
     if (out) {
       TRY(prop_sample(P, smp, o1.p, out, ra, base));
@@ -1570,8 +1654,9 @@ int wp_create(wp_ctx **out, int device, size_t budget) {
       CU(prepare_stencil3d_adj(R, &c->smem3d[1][R], &c->occ3d[1][R], &c->ty3d[1][R]));
     }
     for (int R = 1; R <= 4; ++R) CU(prepare_stencil3d_tb(R, &c->smem_tb[R], &c->occ_tb[R]));
+    for (int R = 1; R <= 4; ++R) CU(prepare_stencil3d_pair(R, &c->smem_pair[R], &c->occ_pair[R]));
     const char *tbe = getenv("WP_TEMPORAL_BLOCKING");
-    c->temporal_blocking = tbe && atoi(tbe) != 0;
+    c->temporal_blocking = tbe ? std::max(0, std::min(2, atoi(tbe))) : 0;
     return WP_OK;
   }();
   if (rc != WP_OK) {
@@ -1606,9 +1691,10 @@ int wp_set_timeout(wp_ctx *c, double seconds) {
   return WP_OK;
 }
 
-int wp_set_temporal_blocking(wp_ctx *c, int enable) {
+int wp_set_temporal_blocking(wp_ctx *c, int mode) {
   if (!c) return fail(WP_EINVAL, "context is NULL");
-  c->temporal_blocking = enable != 0;
+  if (mode < 0 || mode > 2) return fail(WP_EINVAL, "temporal blocking mode must be 0, 1 or 2");
+  c->temporal_blocking = mode;
   return WP_OK;
 }
 

@@ -31,6 +31,12 @@ inline int stencil3d_tile_y(int R, int mode) {
   return mode == 1 ? stencil3d_tile_y_adj(R) : stencil3d_tile_y_fwd(R);
 }
 
+// ---- K1, 3D, two steps by two CTA roles in one cooperative launch (stencil3d_pair.cu) ----
+// maps: u^n halo, u^{n-1} tile, b, s, u^{n+1} halo, u^n tile (the mode-0 boxes); R <= 4
+cudaError_t launch_stencil3d_pair(int R, dim3 grid, cudaStream_t st, const CUtensorMap *maps,
+                                  const Stencil3dArgs &a);
+cudaError_t prepare_stencil3d_pair(int R, int *smem_bytes, int *blocks_per_sm);
+
 // ---- K1, 3D, two steps per launch (stencil3d_tb.cu) ----
 struct Stencil3dTbArgs;
 // Box sizes of the two-step kernel for half-order R (false if R is not covered).

@@ -39,7 +39,18 @@ constexpr int kThreads3d = (kConsumerWarps + 1) * 32;
 constexpr int kFlagTX = 32;                 // x extent of a damping-flag tile
 constexpr int kTileFlagTY = 16;             // y extent of a damping-flag tile
 
-enum StencilMode : int { kModeFwd = 0, kModeAdjGrad = 1 };
+enum StencilMode : int { kModeFwd = 0, kModeAdjGrad = 1, kModePair = 2 };
+
+// Two forward steps by two roles of CTAs in one cooperative launch (kModePair):
+// even CTAs take (u^{n-1}, u^n) -> u^{n+1} exactly as kModeFwd, with the injection
+// of q^n applied at the store, and publish per work item how many planes of u^{n+1}
+// are complete; odd CTAs take (u^n, u^{n+1}) -> u^{n+2} and load a plane of u^{n+1}
+// only once the items that hold it (own column and its four edge neighbours, and
+// the chunk below for the z halo) have published it.  Every CTA is resident and
+// even CTAs never wait, so every awaited item is eventually produced; u^{n+1} is
+// read back from L2 shortly after it is written.
+constexpr int kPairMaxTargets = 64;
+constexpr int kErrWaitPeer = 3;  // a column's progress did not arrive in time
 
 // Tile parameters, chosen by measurement; the -D overrides exist for sweeps.
 #ifndef WP_NX
@@ -71,7 +82,7 @@ enum StencilMode : int { kModeFwd = 0, kModeAdjGrad = 1 };
 template <int R, int MODE>
 struct Cfg3d {
   static constexpr int NX = WP_NX;
-  static constexpr int NY = MODE == kModeFwd ? (R <= 4 ? WP_NY_LO : WP_NY_HI) : 2;
+  static constexpr int NY = MODE != kModeAdjGrad ? (R <= 4 ? WP_NY_LO : WP_NY_HI) : 2;
   static constexpr int TX = 32 * NX;                                 // tile width
   static constexpr int TY = kConsumerWarps * NY;                     // tile height
   static constexpr int RX = (R + 3) / 4 * 4;                         // x halo rounded to 16 bytes
@@ -88,7 +99,8 @@ struct Cfg3d {
   static constexpr int TSLOT = TX * TY * 4;                          // bytes per tile
   static constexpr int T_OFF = NSU * USLOT;
   static constexpr int BAR_OFF = T_OFF + NST * NSTREAM * TSLOT;
-  static constexpr int SMEM = BAR_OFF + 2 * (NSU + NST) * 8 + NST * 4 + 16;
+  static constexpr int TGT_OFF = (BAR_OFF + 2 * (NSU + NST) * 8 + NST * 4 + 16 + 15) / 16 * 16;
+  static constexpr int SMEM = MODE == kModePair ? TGT_OFF + kPairMaxTargets * 16 : BAR_OFF + 2 * (NSU + NST) * 8 + NST * 4 + 16;
   static_assert(RX >= RE, "x halo must cover the x window");
 };
 
@@ -109,6 +121,19 @@ struct Stencil3dArgs {
   // updated box [bx0, bx1) x [by0, by1) x [bz0, bz1) (the whole grid normally; bx0 a
   // multiple of 4); neighbours outside it are read, only points inside are written
   int bx0, by0, bz0, bx1, by1, bz1;
+  // kModePair: out = u^{n+1}, grad = u^{n+2}; progress[column] = planes of u^{n+1}
+  // complete (zeroed before the launch); injection of data row `row` (+ *row_base)
+  // into u^{n+1} with the arithmetic of the injection kernel
+  unsigned *progress;
+  int ntarget;
+  const long long *target;
+  const int *rowptr, *pid;
+  const float *w;
+  const float *data;
+  int npts;
+  const long long *row_base;
+  long long row;
+  const float *b;
 };
 
 // ---- scalar / packed-pair arithmetic -------------------------------------
@@ -152,6 +177,31 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
+  // kModePair: role 0 computes u^{n+1} from (tm_um, tm_u) into out; role 1 computes
+  // u^{n+2} from (tm_g = u^n tile, tm_uj = u^{n+1} halo) into grad
+  const int role = MODE == kModePair ? static_cast<int>(blockIdx.x & 1u) : 0;
+  const int cta = MODE == kModePair ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
+  const int ncta = MODE == kModePair ? static_cast<int>(gridDim.x >> 1) : static_cast<int>(gridDim.x);
+  const CUtensorMap *map_u = (MODE == kModePair && role) ? &tm_uj : &tm_u;
+  const CUtensorMap *map_um = (MODE == kModePair && role) ? &tm_g : &tm_um;
+  float *const outp = (MODE == kModePair && role) ? a.grad : a.out;
+  // role 0: the injection targets of this CTA's column, (z, y, x, increment)
+  float4 *tgt = reinterpret_cast<float4 *>(smem + C::TGT_OFF);
+  __shared__ int ntgt_col;
+  if (MODE == kModePair && role == 0) {
+    // every injection target (z, y, x, increment); the stores check them
+    if (tid == 0) ntgt_col = a.ntarget;
+    if (tid < a.ntarget) {
+      const long long t = a.target[tid];
+      const int z = static_cast<int>(t / a.g.plane);
+      const long long rem = t - static_cast<long long>(z) * a.g.plane;
+      const int y = static_cast<int>(rem / a.g.pitch), x = static_cast<int>(rem - static_cast<long long>(y) * a.g.pitch);
+      const float *qd = a.data + (a.row + (a.row_base ? *a.row_base : 0)) * a.npts;
+      float acc = 0.f;
+      for (int k = a.rowptr[tid]; k < a.rowptr[tid + 1]; ++k) acc = fmaf(a.w[k], qd[a.pid[k]], acc);
+      tgt[tid] = make_float4(__int_as_float(z), __int_as_float(y), __int_as_float(x), __fmul_rn(a.b[t], acc));
+    }
+  }
   if (tid == 0) {
     for (int i = 0; i < C::NSU; ++i) {
       mbar_init(&full_u[i], 1);
@@ -169,7 +219,7 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
   // Items of this CTA, round-robin: in every round the CTAs hold consecutive items
   // (neighbouring tiles and a tile's adjacent z-chunks), so halos meet in L2.
   const int item_end = a.nitems;
-  auto first_item = [&](int i) -> int { return blockIdx.x + i * gridDim.x; };
+  auto first_item = [&](int i) -> int { return cta + i * ncta; };
   auto item_geom = [&](int item, int &tx, int &ty, int &z0, int &z1) {
     const int tile = item / a.nzc, zc = item - tile * a.nzc;
     tx = tile % a.tiles_x;
@@ -181,8 +231,8 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
   if (warp == kConsumerWarps) {
     // ---------------- producer (one lane) ----------------
     if (lane == 0) {
-      prefetch_tensormap(&tm_u);
-      prefetch_tensormap(&tm_um);
+      prefetch_tensormap(map_u);
+      prefetch_tensormap(map_um);
       prefetch_tensormap(&tm_b);
       prefetch_tensormap(&tm_s);
       if (MODE == kModeAdjGrad) {
@@ -200,6 +250,47 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
         ok = false;
         return false;
       };
+      // kModePair, role 1: wait until the items holding plane p of u^{n+1} for the
+      // plane box (this column and its four edge neighbours; own column only when
+      // `own`) have published it
+      // (the last value read per column is kept: progress only grows, and the
+      // producing CTAs usually run ahead, so most planes need no poll)
+      int col_tx = 0, col_ty = 0;
+      int seen_key = -1;      // item (column, chunk) the cached values belong to
+      unsigned seen[5] = {0, 0, 0, 0, 0};
+      auto wait_columns = [&](int p, bool own) -> bool {
+        const int c = (p - a.bz0) / a.zchunk;
+        const unsigned need = static_cast<unsigned>(p - (a.bz0 + c * a.zchunk) + 1);
+        const int key = (col_ty * a.tiles_x + col_tx) * a.nzc + c + (own ? 1 << 30 : 0);
+        if (key != seen_key) {
+          seen_key = key;
+          for (int k = 0; k < 5; ++k) seen[k] = 0;
+        }
+        bool polled = false;
+        const uint64_t t0 = global_timer_ns();
+        for (int k = 0; k < (own ? 1 : 5); ++k) {
+          const int cx = col_tx + (k == 1 ? -1 : k == 2 ? 1 : 0), cy = col_ty + (k == 3 ? -1 : k == 4 ? 1 : 0);
+          if (cx < 0 || cx >= a.tiles_x || cy < 0 || cy >= a.tiles_y) continue;
+          if (seen[k] >= need) continue;
+          polled = true;
+          const unsigned *f = a.progress + (static_cast<long long>(cy) * a.tiles_x + cx) * a.nzc + c;
+          while (true) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+            seen[k] = v;
+            if (v >= need) break;
+            if (*abort_flag) return false;
+            if (global_timer_ns() - t0 > kWaitLimitNs) {
+              atomicCAS(a.err, 0, static_cast<int>(kErrWaitPeer));
+              *abort_flag = 1;
+              return false;
+            }
+          }
+        }
+        // the published planes were written by generic stores; the TMA reads them
+        if (polled) asm volatile("fence.proxy.async.global;" ::: "memory");
+        return true;
+      };
       auto issue_u = [&](int x0, int y0, int p) {
         const uint32_t slot = iu % C::NSU;
         if (iu >= C::NSU && !mbar_wait_bounded(&empty_u[slot], ((iu / C::NSU) - 1) & 1, abort_flag)) {
@@ -208,8 +299,12 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
         }
         float *dst = uring + slot * (C::USLOT / 4);
         if (!aligned(dst, x0 - C::RX)) return;
+        if (MODE == kModePair && role == 1 && p >= a.bz0 && p < a.bz1 && !wait_columns(p, false)) {
+          ok = false;
+          return;
+        }
         mbar_arrive_expect_tx(&full_u[slot], C::PW * C::PH * 4);
-        tma_load_3d(dst, &tm_u, x0 - C::RX, y0 - R, p, &full_u[slot]);
+        tma_load_3d(dst, map_u, x0 - C::RX, y0 - R, p, &full_u[slot]);
         ++iu;
       };
       auto issue_t = [&](int x0, int y0, int z, bool d) {
@@ -223,7 +318,7 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
         sflag[slot] = d ? 1 : 0;  // published by the arrive below (release) to the waiters (acquire)
         const int n = (MODE == kModeAdjGrad ? 4 : 2) + (d ? 1 : 0);
         mbar_arrive_expect_tx(&full_t[slot], n * C::TSLOT);
-        tma_load_3d(t + 0 * TT, &tm_um, x0, y0, z, &full_t[slot]);
+        tma_load_3d(t + 0 * TT, map_um, x0, y0, z, &full_t[slot]);
         tma_load_3d(t + 1 * TT, &tm_b, x0, y0, z, &full_t[slot]);
         if (d) tma_load_3d(t + 2 * TT, &tm_s, x0, y0, z, &full_t[slot]);
         if (MODE == kModeAdjGrad) {
@@ -237,6 +332,16 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
         item_geom(item, tx, ty, z0, z1);
         if (z0 >= z1) continue;
         const int x0 = a.bx0 + tx * TX, y0 = a.by0 + ty * TY;
+        col_tx = tx;
+        col_ty = ty;
+        if (MODE == kModePair && role == 1 && z0 > a.bz0) {  // z halo below: centres read by the consumers
+          bool good = true;
+          for (int p = max(z0 - R, a.bz0); p < z0 && good; ++p) good = wait_columns(p, true);
+          if (!good) {
+            ok = false;
+            break;
+          }
+        }
         // damping bits of the flag tiles covered by this work tile
         const int fx0 = x0 / kFlagTX, fx1 = min((x0 + TX - 1) / kFlagTX + 1, a.flag_tiles_x);
         const int fy0 = y0 / kTileFlagTY, fy1 = min((y0 + TY - 1) / kTileFlagTY + 1, a.flag_tiles_y);
@@ -310,10 +415,17 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
       const int p = z0 - R + j;
 #pragma unroll
       for (int r = 0; r < NY; ++r) {
-        const float *src = a.u + p * a.g.plane + rbase[r];
+        const float *src = (MODE == kModePair && role ? a.out : a.u) + p * a.g.plane + rbase[r];
+        if constexpr (MODE == kModePair) {
+          if (role == 1 && j == 0 && r == 0 && p >= 0)  // the producer has checked the chunk below
+            mbar_wait_bounded(&full_u[ub % C::NSU], (ub / C::NSU) & 1, abort_flag);
+        }
         const bool ok = p >= 0 && yin[r];
         if constexpr (NX == 2) {
-          q[r][j] = make_float2(ok && xin0 ? __ldg(src + gxc0) : 0.f, ok && xin1 ? __ldg(src + gxc1) : 0.f);
+          if (MODE == kModePair && role == 1)  // written by other CTAs of this launch: coherent loads
+            q[r][j] = make_float2(ok && xin0 ? __ldcg(src + gxc0) : 0.f, ok && xin1 ? __ldcg(src + gxc1) : 0.f);
+          else
+            q[r][j] = make_float2(ok && xin0 ? __ldg(src + gxc0) : 0.f, ok && xin1 ? __ldg(src + gxc1) : 0.f);
         } else {
           q[r][j] = ok && xin0 ? __ldg(src + gxc0) : 0.f;
         }
@@ -402,14 +514,26 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
           const V dd = vsub(c, vld<V>(T + ti));
           const V sv = d ? vld<V>(T + 2 * TT + ti) : vsplat<V>(0.f);
           const V bl = vmul(vld<V>(T + TT + ti), lap[r]);
-          const V un = vadd(vfma(sv, dd, vadd(c, dd)), bl);
+          V un = vadd(vfma(sv, dd, vadd(c, dd)), bl);
           V gn = vsplat<V>(0.f);
           if (MODE == kModeAdjGrad)
             gn = vfma(vmul(vsplat<V>(a.neg_inv_dt2), vld<V>(T + 3 * TT + ti)), vfma(sv, dd, bl),
                       vld<V>(T + 4 * TT + ti));
           if (yin[r] && live) {
-            float *o = a.out + po + rbase[r] + gx;
+            float *o = outp + po + rbase[r] + gx;
             float *gp = a.grad + po + rbase[r] + gx;
+            if constexpr (MODE == kModePair) {
+              if (role == 0) {  // q^n injected at its targets, as the injection kernel does
+                const int gy = y0 + ty0 + r;
+                for (int k = 0; k < ntgt_col; ++k) {
+                  const float4 e = tgt[k];
+                  if (__float_as_int(e.x) != z || __float_as_int(e.y) != gy) continue;
+                  const int tx_ = __float_as_int(e.z);
+                  if (tx_ == gx) un.x = __fadd_rn(un.x, e.w);
+                  if (NX == 2 && tx_ == gx + 1) un.y = __fadd_rn(un.y, e.w);
+                }
+              }
+            }
             if constexpr (NX == 2) {
               if (xin1) {
                 *reinterpret_cast<float2 *>(o) = un;
@@ -436,6 +560,20 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
 #pragma unroll
         for (int j = 0; j < 2 * R; ++j) q[r][j] = q[r][j + n];
     };
+    // kModePair, role 0: publish the planes of this column written so far
+    auto publish = [&](int zdone) {
+      if constexpr (MODE == kModePair) {
+        if (role == 0 && (((zdone - z0) & 3) == 0 || zdone == z1)) {  // every four planes and at the end
+          __threadfence();
+          asm volatile("bar.sync 1, %0;" ::"n"(kConsumerWarps * 32) : "memory");
+          if (warp == 0 && lane == 0) {
+            unsigned *f = a.progress + item;
+            const unsigned v = static_cast<unsigned>(zdone - z0);
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(f), "r"(v) : "memory");
+          }
+        }
+      }
+    };
     int z = z0;
     for (; z + C::ZU <= z1; z += C::ZU) {
       plane(z, std::integral_constant<int, 0>{});
@@ -443,10 +581,12 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
       if constexpr (C::ZU > 2) plane(z + 2, std::integral_constant<int, 2>{});
       if constexpr (C::ZU > 3) plane(z + 3, std::integral_constant<int, 3>{});
       rotate(std::integral_constant<int, C::ZU>{});
+      publish(z + C::ZU);
     }
     for (; z < z1; ++z) {
       plane(z, std::integral_constant<int, 0>{});
       rotate(std::integral_constant<int, 1>{});
+      publish(z + 1);
     }
     ub += static_cast<uint32_t>(z1 + R - z0);
   }

@@ -444,8 +444,9 @@ def wp_checkpoint_schedule(nt: int, checkpoints: int):
     return ops, int(fw.value)
 
 
-def wp_set_temporal_blocking(ctx: int, enable: bool) -> None:
-    _check(lib().wp_set_temporal_blocking(ctx, 1 if enable else 0))
+def wp_set_temporal_blocking(ctx: int, mode) -> None:
+    """0: single steps; 1 (or True): two steps per launch on chip; 2: two CTA roles."""
+    _check(lib().wp_set_temporal_blocking(ctx, int(mode)))
 
 
 def wp_trim(ctx: int, keep_bytes: int = 0) -> None:
