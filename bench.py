@@ -60,6 +60,8 @@ def parse():
                    help="timed FWI gradients of the 200^3 + 40 blobs workload (0 skips the gradient leg)")
     p.add_argument("--gradient-nt", type=int, default=1500,
                    help="time steps of the gradient workload (1500; fewer only for profiling)")
+    p.add_argument("--cfd-n", type=int, default=8192,
+                   help="edge of the 2D CFD example fields (0 skips the CFD leg)")
     p.add_argument("--large-nt", type=int, default=3000,
                    help="time steps of the full-size SO16 salt leg (0 skips it)")
     p.add_argument("--checkpoints", type=int, default=20,
@@ -473,6 +475,48 @@ def large_leg(args):
     return out
 
 
+def cfd_leg(args):
+    """The CFD examples of Sec. 5 at GPU scale: 8192^2 fields (67 M points, 256 MB
+    each, larger than L2), convection and Poisson 200 steps, Burgers' equation 100,
+    inputs resident in HBM (device-array calls)."""
+    import torch
+    from paper_1808_01995_gb300 import wavprop as W
+    n = args.cfd_n
+    rng = np.random.default_rng(1808 + 7)
+    dx = dy = 1.0 / (n - 1)
+    u0 = torch.from_numpy(rng.uniform(1.0, 2.0, (n, n)).astype(np.float32)).cuda()
+    v0 = torch.from_numpy(rng.uniform(0.5, 1.5, (n, n)).astype(np.float32)).cuda()
+    b = torch.from_numpy(rng.standard_normal((n, n)).astype(np.float32)).cuda()
+    o1, o2 = torch.empty_like(u0), torch.empty_like(u0)
+    ctx = W.Context(0)
+    h = ctx.handle
+    c, nu = 1.0, 1e-7
+    dt = 0.45 / (c / dx + c / dy)
+    dtb = 0.4 / (2.0 / dx + 2.0 / dy + 2 * nu * (1 / dx**2 + 1 / dy**2))
+    runs = {
+        "convection": (200, 8, lambda k: W.wp_convection_2d_dev(h, u0, dx, dy, dt, c, k, o1)),
+        "burgers": (100, 16, lambda k: W.wp_burgers_2d_dev(h, u0, v0, dx, dy, dtb, nu, k, o1, o2)),
+        "poisson": (200, 12, lambda k: W.wp_poisson_2d_dev(h, u0, b, dx, dy, k, o1)),
+    }
+    peak, _ = measured_peaks()
+    out = {"grid": [n, n], "inputs": "resident in HBM"}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, (steps, bpp, fn) in runs.items():
+        fn(4)  # warm-up (pool, first launches)
+        torch.cuda.synchronize()
+        e0.record()
+        fn(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        pts = float(n) * n * steps
+        gbs = bpp * pts / (ms * 1e-3) / 1e9
+        out[name] = {"steps": steps, "ms": ms, "gpts_per_s": pts / (ms * 1e-3) / 1e9,
+                     "bytes_per_point_step": bpp, "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak}
+    ctx.close()
+    return out
+
+
 def run_ours(args):
     world, rank, local = dist_init()
     import torch
@@ -580,6 +624,10 @@ def run_ours(args):
     if args.large_nt > 0 and world == 1:
         large = large_leg(args)
 
+    cfd = None
+    if args.cfd_n > 0 and world == 1:
+        cfd = cfd_leg(args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, steps, el, nthreads = oracle_sample(model, dt, args.cpu_seconds)
@@ -591,7 +639,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": describe(model, nt, dt),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clk.summary(), "gradient": gradient, "serving": serving, "large": large}
+                "clocks": clk.summary(), "gradient": gradient, "serving": serving, "large": large, "cfd": cfd}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

@@ -258,6 +258,34 @@ void wp_state_free(wp_state *state);
  * which blocks loops in space only. */
 int wp_set_temporal_blocking(wp_ctx *ctx, int mode);
 
+/* ---- The computational-fluid-dynamics examples of Sec. 5 (2D, FP32) --------
+ * Fields are (ny, nx) arrays in C order (x fastest).  Each call advances the
+ * interior points 1 <= i <= nx-2, 1 <= j <= ny-2 and keeps the edge values of the
+ * initial field (Dirichlet data; the paper's examples set them to 1, 1 and 0).
+ * Inputs are read, outputs written by the call; errors as for the propagator
+ * (WP_EINVAL, WP_ENONFINITE for NaN/Inf inputs, WP_ENOMEM, WP_ECUDA).
+ *
+ * Convection (Eq. convection_fd): nt steps of
+ *   u_{i,j} <- u_{i,j} - c dt/dx (u_{i,j} - u_{i-1,j}) - c dt/dy (u_{i,j} - u_{i,j-1});
+ * WP_ECFL unless c >= 0 and c dt/dx + c dt/dy <= 1 (the upwind scheme's limit). */
+int wp_convection_2d(wp_ctx *ctx, int nx, int ny, double dx, double dy, double dt, double c, int nt,
+                     const float *u0, float *u_out);
+/* Burgers' equation (Eq. Burger): nt forward-Euler steps of the coupled system with
+ * upwind (backward) first derivatives and central second derivatives, viscosity nu. */
+int wp_burgers_2d(wp_ctx *ctx, int nx, int ny, double dx, double dy, double dt, double nu, int nt,
+                  const float *u0, const float *v0, float *u_out, float *v_out);
+/* Poisson (Eq. Poisson_fd): nit Jacobi iterations for Lap p = b from p0. */
+int wp_poisson_2d(wp_ctx *ctx, int nx, int ny, double dx, double dy, int nit, const float *p0,
+                  const float *b, float *p_out);
+/* Device-array variants (stream-ordered like the other *_dev calls). */
+int wp_convection_2d_dev(wp_ctx *ctx, int nx, int ny, double dx, double dy, double dt, double c,
+                         int nt, const float *u0, float *u_out, void *stream);
+int wp_burgers_2d_dev(wp_ctx *ctx, int nx, int ny, double dx, double dy, double dt, double nu,
+                      int nt, const float *u0, const float *v0, float *u_out, float *v_out,
+                      void *stream);
+int wp_poisson_2d_dev(wp_ctx *ctx, int nx, int ny, double dx, double dy, int nit, const float *p0,
+                      const float *b, float *p_out, void *stream);
+
 /* Device bytes currently held by the context (including live states). */
 size_t wp_bytes_in_use(const wp_ctx *ctx);
 

@@ -1691,6 +1691,144 @@ int wp_set_timeout(wp_ctx *c, double seconds) {
   return WP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// CFD examples of Sec. 5 (2D, FP32): convection, Burgers' equation, Poisson
+// ---------------------------------------------------------------------------
+static int cfd_args(int nx, int ny, double dx, double dy, int steps) {
+  if (nx < 3 || ny < 3 || nx > (1 << 24) || ny > (1 << 24)) return fail(WP_EINVAL, "nx and ny must be in [3, 2^24]");
+  if (!(dx > 0) || !(dy > 0) || !std::isfinite(dx) || !std::isfinite(dy))
+    return fail(WP_EINVAL, "dx and dy must be positive and finite");
+  if (steps < 0) return fail(WP_EINVAL, "the number of steps must be >= 0");
+  return WP_OK;
+}
+
+// stage n floats from the caller into dst, checking them for NaN/Inf
+static int cfd_stage(wp_ctx *c, float *dst, const float *src, size_t n, bool host_io, const char *what) {
+  if (!src) return fail(WP_EINVAL, "%s is NULL", what);
+  if (host_io) {
+    if (!all_finite(src, n)) return fail(WP_ENONFINITE, "%s holds NaN or Inf", what);
+    CU(cudaMemcpyAsync(dst, src, n * 4, cudaMemcpyHostToDevice, c->stream));
+    return WP_OK;
+  }
+  CU(cudaMemcpyAsync(dst, src, n * 4, cudaMemcpyDeviceToDevice, c->stream));
+  int *bad = c->d_scalars + 1;
+  CU(cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+  CU(launch_check_finite(c->stream, dst, static_cast<long long>(n), bad));
+  c->launches++;
+  CU(cudaMemcpyAsync(c->h_scalars + 1, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  TRY(ctx_wait(c, "input check"));
+  if (c->h_scalars[1]) return fail(WP_ENONFINITE, "%s holds NaN or Inf", what);
+  return WP_OK;
+}
+
+static int convection_impl(wp_ctx *c, int nx, int ny, double dx, double dy, double dt, double cs, int nt,
+                           const float *u0, float *u_out, bool host_io) {
+  TRY(cfd_args(nx, ny, dx, dy, nt));
+  if (!u_out) return fail(WP_EINVAL, "u_out is NULL");
+  if (!(dt >= 0) || !std::isfinite(dt) || !std::isfinite(cs)) return fail(WP_EINVAL, "dt and c must be finite, dt >= 0");
+  const double sx = cs * dt / dx, sy = cs * dt / dy;
+  if (cs < 0 || sx + sy > 1.0 + 1e-12)
+    return fail(WP_ECFL, "upwind convection needs c >= 0 and c dt/dx + c dt/dy <= 1 (got %.6g)", sx + sy);
+  const size_t n = size_t(nx) * ny;
+  Arena ar(c);
+  float *f[2];
+  TRY(ar.alloc(&f[0], n));
+  TRY(ar.alloc(&f[1], n));
+  TRY(cfd_stage(c, f[0], u0, n, host_io, "u0"));
+  for (int k = 0; k < nt; ++k) {
+    CU(launch_convection(c->stream, f[k & 1], f[(k + 1) & 1], nx, ny, float(sx), float(sy)));
+    c->launches++;
+  }
+  CU(cudaMemcpyAsync(u_out, f[nt & 1], n * 4, host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                     c->stream));
+  return ctx_wait(c, "convection");
+}
+
+static int burgers_impl(wp_ctx *c, int nx, int ny, double dx, double dy, double dt, double nu, int nt,
+                        const float *u0, const float *v0, float *u_out, float *v_out, bool host_io) {
+  TRY(cfd_args(nx, ny, dx, dy, nt));
+  if (!u_out || !v_out) return fail(WP_EINVAL, "u_out and v_out must not be NULL");
+  if (!(dt >= 0) || !std::isfinite(dt) || !(nu >= 0) || !std::isfinite(nu))
+    return fail(WP_EINVAL, "dt and nu must be finite and >= 0");
+  const size_t n = size_t(nx) * ny;
+  Arena ar(c);
+  float *uf[2], *vf[2];
+  for (int k = 0; k < 2; ++k) {
+    TRY(ar.alloc(&uf[k], n));
+    TRY(ar.alloc(&vf[k], n));
+  }
+  TRY(cfd_stage(c, uf[0], u0, n, host_io, "u0"));
+  TRY(cfd_stage(c, vf[0], v0, n, host_io, "v0"));
+  for (int k = 0; k < nt; ++k) {
+    CU(launch_burgers(c->stream, uf[k & 1], vf[k & 1], uf[(k + 1) & 1], vf[(k + 1) & 1], nx, ny, float(1.0 / dx),
+                      float(1.0 / dy), float(dt), float(nu / (dx * dx)), float(nu / (dy * dy))));
+    c->launches++;
+  }
+  const cudaMemcpyKind kind = host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  CU(cudaMemcpyAsync(u_out, uf[nt & 1], n * 4, kind, c->stream));
+  CU(cudaMemcpyAsync(v_out, vf[nt & 1], n * 4, kind, c->stream));
+  return ctx_wait(c, "burgers");
+}
+
+static int poisson_impl(wp_ctx *c, int nx, int ny, double dx, double dy, int nit, const float *p0, const float *b,
+                        float *p_out, bool host_io) {
+  TRY(cfd_args(nx, ny, dx, dy, nit));
+  if (!p_out) return fail(WP_EINVAL, "p_out is NULL");
+  const size_t n = size_t(nx) * ny;
+  Arena ar(c);
+  float *f[2], *bd;
+  TRY(ar.alloc(&f[0], n));
+  TRY(ar.alloc(&f[1], n));
+  TRY(ar.alloc(&bd, n));
+  TRY(cfd_stage(c, f[0], p0, n, host_io, "p0"));
+  TRY(cfd_stage(c, bd, b, n, host_io, "b"));
+  const double dx2 = dx * dx, dy2 = dy * dy;
+  for (int k = 0; k < nit; ++k) {
+    CU(launch_poisson(c->stream, f[k & 1], bd, f[(k + 1) & 1], nx, ny, float(dx2), float(dy2),
+                      float(1.0 / (2.0 * (dx2 + dy2)))));
+    c->launches++;
+  }
+  CU(cudaMemcpyAsync(p_out, f[nit & 1], n * 4, host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                     c->stream));
+  return ctx_wait(c, "poisson");
+}
+
+int wp_convection_2d(wp_ctx *c, int nx, int ny, double dx, double dy, double dt, double cs, int nt, const float *u0,
+                     float *u_out) {
+  TRY(enter(c, nullptr));
+  return leave(c, nullptr, convection_impl(c, nx, ny, dx, dy, dt, cs, nt, u0, u_out, true));
+}
+
+int wp_convection_2d_dev(wp_ctx *c, int nx, int ny, double dx, double dy, double dt, double cs, int nt,
+                         const float *u0, float *u_out, void *stream) {
+  TRY(enter(c, stream));
+  return leave(c, stream, convection_impl(c, nx, ny, dx, dy, dt, cs, nt, u0, u_out, false));
+}
+
+int wp_burgers_2d(wp_ctx *c, int nx, int ny, double dx, double dy, double dt, double nu, int nt, const float *u0,
+                  const float *v0, float *u_out, float *v_out) {
+  TRY(enter(c, nullptr));
+  return leave(c, nullptr, burgers_impl(c, nx, ny, dx, dy, dt, nu, nt, u0, v0, u_out, v_out, true));
+}
+
+int wp_burgers_2d_dev(wp_ctx *c, int nx, int ny, double dx, double dy, double dt, double nu, int nt, const float *u0,
+                      const float *v0, float *u_out, float *v_out, void *stream) {
+  TRY(enter(c, stream));
+  return leave(c, stream, burgers_impl(c, nx, ny, dx, dy, dt, nu, nt, u0, v0, u_out, v_out, false));
+}
+
+int wp_poisson_2d(wp_ctx *c, int nx, int ny, double dx, double dy, int nit, const float *p0, const float *b,
+                  float *p_out) {
+  TRY(enter(c, nullptr));
+  return leave(c, nullptr, poisson_impl(c, nx, ny, dx, dy, nit, p0, b, p_out, true));
+}
+
+int wp_poisson_2d_dev(wp_ctx *c, int nx, int ny, double dx, double dy, int nit, const float *p0, const float *b,
+                      float *p_out, void *stream) {
+  TRY(enter(c, stream));
+  return leave(c, stream, poisson_impl(c, nx, ny, dx, dy, nit, p0, b, p_out, false));
+}
+
 int wp_set_temporal_blocking(wp_ctx *c, int mode) {
   if (!c) return fail(WP_EINVAL, "context is NULL");
   if (mode < 0 || mode > 2) return fail(WP_EINVAL, "temporal blocking mode must be 0, 1 or 2");

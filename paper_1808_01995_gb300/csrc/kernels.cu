@@ -488,3 +488,232 @@ cudaError_t launch_add_row(cudaStream_t st, long long *p, long long d) {
 }
 
 }  // namespace wp
+
+namespace wp {
+
+// ---------------------------------------------------------------------------
+// CFD examples (Sec. 5), 2D fields (ny, nx), x fastest; the interior points are
+// updated, the edge values (Dirichlet data) are copied through.
+// ---------------------------------------------------------------------------
+__global__ void convection_kernel(const float *__restrict__ u, float *__restrict__ out, int nx, int ny, float sx,
+                                  float sy) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+  for (int j = blockIdx.y; j < ny; j += gridDim.y) {
+    const long long k = static_cast<long long>(j) * nx + i;
+    const float c = u[k];
+    if (i == 0 || j == 0 || i == nx - 1 || j == ny - 1) {
+      out[k] = c;
+      continue;
+    }
+    // Eq. convection_fd: backward differences in x and y
+    out[k] = c - sx * (c - __ldg(u + k - 1)) - sy * (c - __ldg(u + k - nx));
+  }
+}
+
+__global__ void burgers_kernel(const float *__restrict__ u, const float *__restrict__ v, float *__restrict__ uo,
+                               float *__restrict__ vo, int nx, int ny, float rdx, float rdy, float dt, float nudx2,
+                               float nudy2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+  for (int j = blockIdx.y; j < ny; j += gridDim.y) {
+    const long long k = static_cast<long long>(j) * nx + i;
+    const float uc = u[k], vc = v[k];
+    if (i == 0 || j == 0 || i == nx - 1 || j == ny - 1) {
+      uo[k] = uc;
+      vo[k] = vc;
+      continue;
+    }
+    const float uw = __ldg(u + k - 1), ue = __ldg(u + k + 1), us = __ldg(u + k - nx), un = __ldg(u + k + nx);
+    const float vw = __ldg(v + k - 1), ve = __ldg(v + k + 1), vs = __ldg(v + k - nx), vn = __ldg(v + k + nx);
+    // Eq. Burger: upwind (backward) advection, central diffusion, forward Euler
+    const float adv_u = uc * (uc - uw) * rdx + vc * (uc - us) * rdy;
+    const float adv_v = uc * (vc - vw) * rdx + vc * (vc - vs) * rdy;
+    const float lap_u = (ue - 2.f * uc + uw) * nudx2 + (un - 2.f * uc + us) * nudy2;
+    const float lap_v = (ve - 2.f * vc + vw) * nudx2 + (vn - 2.f * vc + vs) * nudy2;
+    uo[k] = uc - dt * adv_u + dt * lap_u;
+    vo[k] = vc - dt * adv_v + dt * lap_v;
+  }
+}
+
+__global__ void poisson_kernel(const float *__restrict__ p, const float *__restrict__ b, float *__restrict__ out,
+                               int nx, int ny, float dx2, float dy2, float inv_den) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+  for (int j = blockIdx.y; j < ny; j += gridDim.y) {
+    const long long k = static_cast<long long>(j) * nx + i;
+    if (i == 0 || j == 0 || i == nx - 1 || j == ny - 1) {
+      out[k] = p[k];
+      continue;
+    }
+    // Eq. Poisson_fd (Jacobi)
+    const float sx = __ldg(p + k + 1) + __ldg(p + k - 1), sy = __ldg(p + k + nx) + __ldg(p + k - nx);
+    out[k] = (sx * dy2 + sy * dx2 - __ldg(b + k) * dx2 * dy2) * inv_den;
+  }
+}
+
+static dim3 cfd_grid(int nx, int ny) {
+  return dim3(static_cast<unsigned>((nx + 255) / 256), static_cast<unsigned>(ny < 65535 ? ny : 65535));
+}
+
+// Streaming forms (nx a multiple of 4): a thread owns four x points (16-byte
+// loads and stores) and walks a strip of kStrip rows, keeping the rows above and
+// below in registers; x neighbours come from the adjacent lanes (shuffles), the
+// warp's outer ones from a scalar load.  Every value is read from DRAM about once.
+constexpr int kStrip = 32;
+
+struct Row4 {
+  float4 v;
+  float w, e;  // x neighbours of the first and last point
+};
+
+__device__ __forceinline__ Row4 load_row4(const float *f, long long row, int x4, int nx, bool in) {
+  Row4 r;
+  r.v = in ? __ldg(reinterpret_cast<const float4 *>(f + row + x4)) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const int lane = threadIdx.x & 31;
+  float w = __shfl_up_sync(0xffffffffu, r.v.w, 1);
+  float e = __shfl_down_sync(0xffffffffu, r.v.x, 1);
+  if (lane == 0) w = (in && x4 > 0) ? __ldg(f + row + x4 - 1) : 0.f;
+  if (lane == 31) e = (in && x4 + 4 < nx) ? __ldg(f + row + x4 + 4) : 0.f;
+  r.w = w;
+  r.e = e;
+  return r;
+}
+
+__device__ __forceinline__ float get4(const float4 &v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+__device__ __forceinline__ void set4(float4 &v, int k, float a) {
+  if (k == 0) v.x = a; else if (k == 1) v.y = a; else if (k == 2) v.z = a; else v.w = a;
+}
+
+__global__ void convection4_kernel(const float *__restrict__ u, float *__restrict__ out, int nx, int ny, float sx,
+                                   float sy) {
+  const int x4 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const bool in = x4 < nx;
+  const int j0 = blockIdx.y * kStrip, j1 = min(j0 + kStrip, ny);
+  float4 up = (in && j0 > 0) ? __ldg(reinterpret_cast<const float4 *>(u + static_cast<long long>(j0 - 1) * nx + x4))
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int j = j0; j < j1; ++j) {
+    const long long row = static_cast<long long>(j) * nx;
+    const Row4 c = load_row4(u, row, x4, nx, in);
+    float4 o = c.v;
+    if (j > 0 && j < ny - 1) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int x = x4 + k;
+        if (x == 0 || x == nx - 1) continue;
+        const float cc = get4(c.v, k), wv = k == 0 ? c.w : get4(c.v, k - 1);
+        set4(o, k, cc - sx * (cc - wv) - sy * (cc - get4(up, k)));
+      }
+    }
+    if (in) *reinterpret_cast<float4 *>(out + row + x4) = o;
+    up = c.v;
+  }
+}
+
+__global__ void burgers4_kernel(const float *__restrict__ u, const float *__restrict__ v, float *__restrict__ uo,
+                                float *__restrict__ vo, int nx, int ny, float rdx, float rdy, float dt, float nudx2,
+                                float nudy2) {
+  const int x4 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const bool in = x4 < nx;
+  const int j0 = blockIdx.y * kStrip, j1 = min(j0 + kStrip, ny);
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto ld = [&](const float *f, int j) -> float4 {
+    return (in && j >= 0 && j < ny) ? __ldg(reinterpret_cast<const float4 *>(f + static_cast<long long>(j) * nx + x4)) : z4;
+  };
+  float4 us = ld(u, j0 - 1), vs = ld(v, j0 - 1);
+  Row4 uc = load_row4(u, static_cast<long long>(j0) * nx, x4, nx, in && j0 < ny);
+  Row4 vc = load_row4(v, static_cast<long long>(j0) * nx, x4, nx, in && j0 < ny);
+  for (int j = j0; j < j1; ++j) {
+    const long long row = static_cast<long long>(j) * nx;
+    const bool has_n = j + 1 < ny;
+    const Row4 un = load_row4(u, row + nx, x4, nx, in && has_n), vn = load_row4(v, row + nx, x4, nx, in && has_n);
+    float4 ou = uc.v, ov = vc.v;
+    if (j > 0 && j < ny - 1) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int x = x4 + k;
+        if (x == 0 || x == nx - 1) continue;
+        const float ucc = get4(uc.v, k), vcc = get4(vc.v, k);
+        const float uw = k == 0 ? uc.w : get4(uc.v, k - 1), ue = k == 3 ? uc.e : get4(uc.v, k + 1);
+        const float vw = k == 0 ? vc.w : get4(vc.v, k - 1), ve = k == 3 ? vc.e : get4(vc.v, k + 1);
+        const float uss = get4(us, k), unn = get4(un.v, k), vss = get4(vs, k), vnn = get4(vn.v, k);
+        const float adv_u = ucc * (ucc - uw) * rdx + vcc * (ucc - uss) * rdy;
+        const float adv_v = ucc * (vcc - vw) * rdx + vcc * (vcc - vss) * rdy;
+        const float lap_u = (ue - 2.f * ucc + uw) * nudx2 + (unn - 2.f * ucc + uss) * nudy2;
+        const float lap_v = (ve - 2.f * vcc + vw) * nudx2 + (vnn - 2.f * vcc + vss) * nudy2;
+        set4(ou, k, ucc - dt * adv_u + dt * lap_u);
+        set4(ov, k, vcc - dt * adv_v + dt * lap_v);
+      }
+    }
+    if (in) {
+      *reinterpret_cast<float4 *>(uo + row + x4) = ou;
+      *reinterpret_cast<float4 *>(vo + row + x4) = ov;
+    }
+    us = uc.v;
+    vs = vc.v;
+    uc = un;
+    vc = vn;
+  }
+}
+
+__global__ void poisson4_kernel(const float *__restrict__ p, const float *__restrict__ b, float *__restrict__ out,
+                                int nx, int ny, float dx2, float dy2, float inv_den) {
+  const int x4 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const bool in = x4 < nx;
+  const int j0 = blockIdx.y * kStrip, j1 = min(j0 + kStrip, ny);
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 ps = (in && j0 > 0) ? __ldg(reinterpret_cast<const float4 *>(p + static_cast<long long>(j0 - 1) * nx + x4)) : z4;
+  Row4 pc = load_row4(p, static_cast<long long>(j0) * nx, x4, nx, in && j0 < ny);
+  const float dxy = dx2 * dy2;
+  for (int j = j0; j < j1; ++j) {
+    const long long row = static_cast<long long>(j) * nx;
+    const Row4 pn = load_row4(p, row + nx, x4, nx, in && j + 1 < ny);
+    float4 o = pc.v;
+    if (j > 0 && j < ny - 1) {
+      const float4 bb = in ? __ldg(reinterpret_cast<const float4 *>(b + row + x4)) : z4;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int x = x4 + k;
+        if (x == 0 || x == nx - 1) continue;
+        const float pw = k == 0 ? pc.w : get4(pc.v, k - 1), pe = k == 3 ? pc.e : get4(pc.v, k + 1);
+        const float sxx = pe + pw, syy = get4(pn.v, k) + get4(ps, k);
+        set4(o, k, (sxx * dy2 + syy * dx2 - get4(bb, k) * dxy) * inv_den);
+      }
+    }
+    if (in) *reinterpret_cast<float4 *>(out + row + x4) = o;
+    ps = pc.v;
+    pc = pn;
+  }
+}
+
+static dim3 cfd_grid4(int nx, int ny) {
+  return dim3(static_cast<unsigned>((nx / 4 + 127) / 128), static_cast<unsigned>((ny + kStrip - 1) / kStrip));
+}
+
+cudaError_t launch_convection(cudaStream_t st, const float *u, float *out, int nx, int ny, float sx, float sy) {
+  if (nx % 4 == 0 && (ny + kStrip - 1) / kStrip <= 65535)
+    convection4_kernel<<<cfd_grid4(nx, ny), 128, 0, st>>>(u, out, nx, ny, sx, sy);
+  else
+    convection_kernel<<<cfd_grid(nx, ny), 256, 0, st>>>(u, out, nx, ny, sx, sy);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_burgers(cudaStream_t st, const float *u, const float *v, float *uo, float *vo, int nx, int ny,
+                           float rdx, float rdy, float dt, float nudx2, float nudy2) {
+  if (nx % 4 == 0 && (ny + kStrip - 1) / kStrip <= 65535)
+    burgers4_kernel<<<cfd_grid4(nx, ny), 128, 0, st>>>(u, v, uo, vo, nx, ny, rdx, rdy, dt, nudx2, nudy2);
+  else
+    burgers_kernel<<<cfd_grid(nx, ny), 256, 0, st>>>(u, v, uo, vo, nx, ny, rdx, rdy, dt, nudx2, nudy2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_poisson(cudaStream_t st, const float *p, const float *b, float *out, int nx, int ny, float dx2,
+                           float dy2, float inv_den) {
+  if (nx % 4 == 0 && (ny + kStrip - 1) / kStrip <= 65535)
+    poisson4_kernel<<<cfd_grid4(nx, ny), 128, 0, st>>>(p, b, out, nx, ny, dx2, dy2, inv_den);
+  else
+    poisson_kernel<<<cfd_grid(nx, ny), 256, 0, st>>>(p, b, out, nx, ny, dx2, dy2, inv_den);
+  return cudaGetLastError();
+}
+
+}  // namespace wp

@@ -168,6 +168,17 @@ cudaError_t launch_ring_copy(cudaStream_t st, float *field, FieldGeom g, float *
 // field = 0 at every point outside `b` (pitched field)
 cudaError_t launch_zero_outside(cudaStream_t st, float *field, FieldGeom g, Box b);
 
+// ---- CFD examples of Sec. 5 (kernels.cu): one step / iteration on (ny, nx) fields,
+// interior updated, edges copied (Dirichlet data) ----
+// convection (Eq. convection_fd), sx = c dt/dx, sy = c dt/dy
+cudaError_t launch_convection(cudaStream_t st, const float *u, float *out, int nx, int ny, float sx, float sy);
+// Burgers' equation (Eq. Burger): rdx = 1/dx, rdy = 1/dy, nudx2 = nu/dx^2, nudy2 = nu/dy^2
+cudaError_t launch_burgers(cudaStream_t st, const float *u, const float *v, float *uo, float *vo, int nx, int ny,
+                           float rdx, float rdy, float dt, float nudx2, float nudy2);
+// Poisson (Eq. Poisson_fd), one Jacobi iteration; inv_den = 1 / (2 (dx^2 + dy^2))
+cudaError_t launch_poisson(cudaStream_t st, const float *p, const float *b, float *out, int nx, int ny, float dx2,
+                           float dy2, float inv_den);
+
 // bit 0 of *bad set if any of x[0..n) is NaN or Inf
 cudaError_t launch_check_finite(cudaStream_t st, const float *x, long long n, int *bad);
 

@@ -32,6 +32,8 @@ EXPORTED = [
     "wp_fwi_gradient", "wp_fwi_gradient_dev", "wp_trim", "wp_set_budget", "wp_axpy_dev",
     "wp_update_model_dev", "wp_gradient_checkpointed", "wp_gradient_checkpointed_dev", "wp_checkpoint_schedule",
     "wp_gradient_reconstruct", "wp_gradient_reconstruct_dev", "wp_set_temporal_blocking",
+    "wp_convection_2d", "wp_convection_2d_dev", "wp_burgers_2d", "wp_burgers_2d_dev", "wp_poisson_2d",
+    "wp_poisson_2d_dev",
 ]
 
 
@@ -87,6 +89,7 @@ _gp = ctypes.POINTER(wp_grid)
 _i = ctypes.c_int
 _fp = ctypes.c_void_p  # float* (host or device address)
 _dp = ctypes.c_void_p  # double* (host)
+_d = ctypes.c_double
 
 
 def lib() -> ctypes.CDLL:
@@ -131,6 +134,12 @@ def lib() -> ctypes.CDLL:
         "wp_gradient_checkpointed": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _fp, _i, _dp, _i, _fp], _i),
         "wp_gradient_checkpointed_dev": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _fp, _i, _dp, _i, _fp, _vp], _i),
         "wp_set_temporal_blocking": ([_vp, _i], _i),
+        "wp_convection_2d": ([_vp, _i, _i, _d, _d, _d, _d, _i, _fp, _fp], _i),
+        "wp_convection_2d_dev": ([_vp, _i, _i, _d, _d, _d, _d, _i, _fp, _fp, _vp], _i),
+        "wp_burgers_2d": ([_vp, _i, _i, _d, _d, _d, _d, _i, _fp, _fp, _fp, _fp], _i),
+        "wp_burgers_2d_dev": ([_vp, _i, _i, _d, _d, _d, _d, _i, _fp, _fp, _fp, _fp, _vp], _i),
+        "wp_poisson_2d": ([_vp, _i, _i, _d, _d, _i, _fp, _fp, _fp], _i),
+        "wp_poisson_2d_dev": ([_vp, _i, _i, _d, _d, _i, _fp, _fp, _fp, _vp], _i),
         "wp_gradient_reconstruct": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _fp, _i, _dp, _fp], _i),
         "wp_gradient_reconstruct_dev": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _fp, _i, _dp, _fp, _vp], _i),
         "wp_checkpoint_schedule": ([_i, _i, _vp, _i, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_longlong)], _i),
@@ -447,6 +456,63 @@ def wp_checkpoint_schedule(nt: int, checkpoints: int):
 def wp_set_temporal_blocking(ctx: int, mode) -> None:
     """0: single steps; 1 (or True): two steps per launch on chip; 2: two CTA roles."""
     _check(lib().wp_set_temporal_blocking(ctx, int(mode)))
+
+
+# ---------------------------------------------------------------------------
+# CFD examples (2D fields (ny, nx))
+# ---------------------------------------------------------------------------
+def _f32_2d(a, what):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.ndim != 2:
+        raise ValueError(f"{what} must be a 2D (ny, nx) array")
+    return a
+
+
+def wp_convection_2d(ctx: int, u0, dx: float, dy: float, dt: float, c: float, nt: int) -> np.ndarray:
+    u0 = _f32_2d(u0, "u0")
+    out = np.empty_like(u0)
+    ny, nx = u0.shape
+    _check(lib().wp_convection_2d(ctx, nx, ny, dx, dy, dt, c, int(nt), _ptr(u0), _ptr(out)))
+    return out
+
+
+def wp_convection_2d_dev(ctx: int, u0, dx, dy, dt, c, nt, u_out, stream=None) -> None:
+    ny, nx = u0.shape
+    _check(lib().wp_convection_2d_dev(ctx, nx, ny, dx, dy, dt, c, int(nt), _ptr(_dev_f32(u0, "u0")),
+                                      _ptr(_dev_f32(u_out, "u_out")), _stream(stream)))
+
+
+def wp_burgers_2d(ctx: int, u0, v0, dx: float, dy: float, dt: float, nu: float, nt: int):
+    u0, v0 = _f32_2d(u0, "u0"), _f32_2d(v0, "v0")
+    if u0.shape != v0.shape:
+        raise ValueError("u0 and v0 must have the same shape")
+    uo, vo = np.empty_like(u0), np.empty_like(v0)
+    ny, nx = u0.shape
+    _check(lib().wp_burgers_2d(ctx, nx, ny, dx, dy, dt, nu, int(nt), _ptr(u0), _ptr(v0), _ptr(uo), _ptr(vo)))
+    return uo, vo
+
+
+def wp_burgers_2d_dev(ctx: int, u0, v0, dx, dy, dt, nu, nt, u_out, v_out, stream=None) -> None:
+    ny, nx = u0.shape
+    _check(lib().wp_burgers_2d_dev(ctx, nx, ny, dx, dy, dt, nu, int(nt), _ptr(_dev_f32(u0, "u0")),
+                                   _ptr(_dev_f32(v0, "v0")), _ptr(_dev_f32(u_out, "u_out")),
+                                   _ptr(_dev_f32(v_out, "v_out")), _stream(stream)))
+
+
+def wp_poisson_2d(ctx: int, p0, b, dx: float, dy: float, nit: int) -> np.ndarray:
+    p0, b = _f32_2d(p0, "p0"), _f32_2d(b, "b")
+    if p0.shape != b.shape:
+        raise ValueError("p0 and b must have the same shape")
+    out = np.empty_like(p0)
+    ny, nx = p0.shape
+    _check(lib().wp_poisson_2d(ctx, nx, ny, dx, dy, int(nit), _ptr(p0), _ptr(b), _ptr(out)))
+    return out
+
+
+def wp_poisson_2d_dev(ctx: int, p0, b, dx, dy, nit, p_out, stream=None) -> None:
+    ny, nx = p0.shape
+    _check(lib().wp_poisson_2d_dev(ctx, nx, ny, dx, dy, int(nit), _ptr(_dev_f32(p0, "p0")), _ptr(_dev_f32(b, "b")),
+                                   _ptr(_dev_f32(p_out, "p_out")), _stream(stream)))
 
 
 def wp_trim(ctx: int, keep_bytes: int = 0) -> None:
