@@ -320,3 +320,27 @@ def test_full_size_dot_test(ctx, layers_so8):
     err = abs(a - b) / abs(a)
     print(f"336^3 SO8 nt={nt}: dot test {err:.3e}")
     assert err < 1e-5
+
+
+@pytest.mark.parametrize("k", [8, 4, 16])
+def test_full_size_forward_matches_oracle(ctx, k):
+    """The benchmark's shot exactly: 336^3, 1000 steps, 16384 off-grid receivers,
+    the device-array call the benchmark times; every trace against the FP64 oracle
+    run over the whole grid (a few tens of seconds on the host cores)."""
+    model = synth.layers_3d(space_order=k)
+    dt = 0.9 * O.cfl_dt(model.spacing, k, model.vmax)
+    nt = model.nt
+    og, wg = grids(model, dt, nt, k)
+    m32, e32 = model.m32(), model.eta32()
+    q = model.wavelet(dt, nt)
+    out = torch.zeros((nt, len(model.rec)), device="cuda")
+    W.wp_forward_dev(ctx, wg, dev(m32), dev(e32), dev(q), model.src, model.rec, out)
+    got = out.cpu().numpy()
+    ref = O.forward(og, m32, e32, q, model.src, model.rec)
+    err = rel_l2(got, ref)
+    # the traces nearest the source carry most of the energy; check the far ones too
+    far = np.argsort(np.linalg.norm(ref, axis=0))[: len(model.rec) // 2]
+    err_far = rel_l2(got[:, far], ref[:, far])
+    print(f"336^3 SO{k} nt={nt}: rel L2 {err:.3e} (weaker half of the traces {err_far:.3e})")
+    assert err < 1e-4
+    assert err_far < 1e-4
