@@ -23,7 +23,10 @@
 // rows: it loads its column of the plane once for all y neighbours, reads x
 // neighbours from the plane and keeps z neighbours in a register queue.  This
 // keeps both the shared-memory traffic and the instructions issued per point
-// low enough for HBM to be the bound.
+// low enough for HBM to be the bound.  Orders above 8 (one CTA per SM, the u ring
+// being R + 1 + P halo'd planes deep) take three rows per lane, three planes in
+// flight and x/y/z partial sums of the Laplacian, for more independent work per
+// warp: those kernels are bound by issue latency, not by HBM.
 // Every wait is bounded (%globaltimer); a timeout sets an abort flag, the
 // producer lets its copies land, and the error word reports it.
 #pragma once
@@ -60,10 +63,10 @@ constexpr int kErrWaitPeer = 3;  // a column's progress did not arrive in time
 #define WP_NY_LO 2       // rows per lane, R <= 4
 #endif
 #ifndef WP_NY_HI
-#define WP_NY_HI 2       // rows per lane, R > 4
+#define WP_NY_HI 3       // rows per lane, R > 4
 #endif
 #ifndef WP_P_HI
-#define WP_P_HI 2        // planes in flight, R > 4
+#define WP_P_HI 3        // planes in flight, R > 4
 #endif
 #ifndef WP_MINB_HI
 #define WP_MINB_HI 1     // CTAs per SM the compiler must fit, R > 4
@@ -76,6 +79,9 @@ constexpr int kErrWaitPeer = 3;  // a column's progress did not arrive in time
 #endif
 #ifndef WP_P_ADJ
 #define WP_P_ADJ 2       // planes in flight, adjoint+gradient mode, R <= 4 (two CTAs per SM)
+#endif
+#ifndef WP_LAP_SPLIT
+#define WP_LAP_SPLIT 1   // R > 4: accumulate the Laplacian in three partial sums (x, y, z)
 #endif
 
 
@@ -92,6 +98,7 @@ struct Cfg3d {
   static constexpr int P = R > 4 ? WP_P_HI : MODE == kModeAdjGrad ? WP_P_ADJ : 3;  // planes in flight ahead
   static constexpr int MINB = R <= 4 ? WP_MINB_LO : WP_MINB_HI;      // CTAs per SM to fit
   static constexpr int ZU = WP_ZU;                                   // planes per unrolled z step
+  static constexpr bool SPLIT = R > 4 && WP_LAP_SPLIT != 0;           // x, y, z partial sums
   static constexpr int NSU = R + 1 + P;                              // u ring depth
   static constexpr int NST = P + 1;                                  // tile ring depth
   static constexpr int NSTREAM = MODE == kModeAdjGrad ? 5 : 3;       // um, b, s [, uj, g]
@@ -467,6 +474,9 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
 #pragma unroll
           for (int r = 0; r < NY; ++r) {
             const float *pc = P + (ty0 + r + R) * C::PW + cx0;
+            // sums of the symmetric neighbour pairs at distance j along x, y, z
+            auto ysum = [&](int j) -> V { return vadd(col[R + r + j], col[R + r - j]); };
+            auto zsum = [&](int j) -> V { return vadd(q[r][o + R + j], q[r][o + R - j]); };
             V l = vmul(vsplat<V>(a.c.c0), q[r][o + R]);
             if constexpr (NX == 2) {
               // window w[k] = columns (cx0 - RE + 2k, +1): point 0 sits at RE, point 1 at RE + 1
@@ -474,24 +484,37 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
 #pragma unroll
               for (int k = 0; k <= C::RE; ++k) w[k] = vld<float2>(pc - C::RE + 2 * k);
               auto win = [&](int i) -> float { return (i & 1) ? w[i >> 1].y : w[i >> 1].x; };
+              auto xsum = [&](int j) -> float2 {
+                if ((j & 1) == 0) return __fadd2_rn(w[(C::RE + j) >> 1], w[(C::RE - j) >> 1]);
+                return make_float2(win(C::RE + j) + win(C::RE - j), win(C::RE + 1 + j) + win(C::RE + 1 - j));
+              };
+              if constexpr (C::SPLIT) {
+                // three partial sums (x, y, z) so that no chain of dependent FMAs is longer than R
+                V ly = vmul(vsplat<V>(a.c.cy[1]), ysum(1));
+                V lz = vmul(vsplat<V>(a.c.cz[1]), zsum(1));
 #pragma unroll
-              for (int j = 1; j <= R; ++j) {
-                float2 xs;
-                if ((j & 1) == 0) {
-                  xs = __fadd2_rn(w[(C::RE + j) >> 1], w[(C::RE - j) >> 1]);
-                } else {
-                  xs = make_float2(win(C::RE + j) + win(C::RE - j), win(C::RE + 1 + j) + win(C::RE + 1 - j));
+                for (int j = 1; j <= R; ++j) {
+                  l = vfma(vsplat<V>(a.c.cx[j]), xsum(j), l);
+                  if (j > 1) {
+                    ly = vfma(vsplat<V>(a.c.cy[j]), ysum(j), ly);
+                    lz = vfma(vsplat<V>(a.c.cz[j]), zsum(j), lz);
+                  }
                 }
-                l = vfma(vsplat<V>(a.c.cx[j]), xs, l);
-                l = vfma(vsplat<V>(a.c.cy[j]), vadd(col[R + r + j], col[R + r - j]), l);
-                l = vfma(vsplat<V>(a.c.cz[j]), vadd(q[r][o + R + j], q[r][o + R - j]), l);
+                l = vadd(l, vadd(ly, lz));
+              } else {
+#pragma unroll
+                for (int j = 1; j <= R; ++j) {
+                  l = vfma(vsplat<V>(a.c.cx[j]), xsum(j), l);
+                  l = vfma(vsplat<V>(a.c.cy[j]), ysum(j), l);
+                  l = vfma(vsplat<V>(a.c.cz[j]), zsum(j), l);
+                }
               }
             } else {
 #pragma unroll
               for (int j = 1; j <= R; ++j) {
                 l = vfma(vsplat<V>(a.c.cx[j]), vadd(vld<V>(pc + j), vld<V>(pc - j)), l);
-                l = vfma(vsplat<V>(a.c.cy[j]), vadd(col[R + r + j], col[R + r - j]), l);
-                l = vfma(vsplat<V>(a.c.cz[j]), vadd(q[r][o + R + j], q[r][o + R - j]), l);
+                l = vfma(vsplat<V>(a.c.cy[j]), ysum(j), l);
+                l = vfma(vsplat<V>(a.c.cz[j]), zsum(j), l);
               }
             }
             lap[r] = l;
