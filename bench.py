@@ -15,6 +15,10 @@ roofline: the stencil kernel's compulsory bytes per launch over its live average
          duration (CUDA events on the library's stream), against the measured
          HBM copy bandwidth.
 cpu_baseline / --impl reference: the FP64 CPU oracle on a bounded sample.
+Further single-GPU legs: the FWI gradient (280^3), shot serving, the 592x592x480
+SO16 workload, the CFD examples and paper_context (the paper's time-to-solution
+experiment: 1000 ms of modelling at SO16 on a 512^3 grid, quoted beside the
+paper's CPU figure as context only).
 
 Multi-GPU (torchrun): replicas only (one independent shot per GPU, no collective).
 """
@@ -64,6 +68,9 @@ def parse():
                    help="edge of the 2D CFD example fields (0 skips the CFD leg)")
     p.add_argument("--large-nt", type=int, default=3000,
                    help="time steps of the full-size SO16 salt leg (0 skips it)")
+    p.add_argument("--context", type=lambda v: [int(x) for x in v.split(",") if x.strip() and int(x) > 0],
+                   default=[512], help="grid edges of the paper-context leg (SO16, 1000 ms of modelling); "
+                   "'0' skips it")
     p.add_argument("--checkpoints", type=int, default=20,
                    help="stored states of the binomial-checkpointing gradient timed beside it (0 skips it)")
     p.add_argument("--no-full-history", dest="full_history", action="store_false",
@@ -475,6 +482,55 @@ def large_leg(args):
     return out
 
 
+# The paper's time-to-solution experiment (Sec. 6.2): 1000 ms of modelling at space
+# order 16 on an Intel Skylake 8180 (28 cores, 2.5 GHz, STREAM TRIAD 105 GB/s).  The
+# paper states neither the velocity model nor dt, so the step counts may differ:
+# context, not a baseline.
+PAPER_TIME_TO_SOLUTION_S = {512: 17.1, 1024: 162.6}
+
+
+def paper_context_leg(args):
+    """Time to solution of 1000 ms of modelling at SO16 on n^3 grids (n = 512 by
+    default; the 40-point damping layer included in n), the layered model of the
+    stencil sweep, dt = 0.9 x CFL, one forward shot (coefficients, stencil,
+    injection, 128 x 128 receivers), inputs resident in HBM, timed after one
+    warm-up shot."""
+    import torch
+    from paper_1808_01995_gb300 import synth
+    from paper_1808_01995_gb300 import wavprop as W
+    out = []
+    for n in args.context:
+        torch.cuda.empty_cache()
+        k, nbl = 16, 40
+        model = synth.layers_3d(space_order=k, n=n - 2 * nbl, nbl=nbl)
+        dt_max = W.wp_cfl_dt(W.Grid(model.shape, model.spacing, model.origin, k), model.vmax)
+        nt = int(math.ceil(1.0 / (0.9 * dt_max)))
+        dt = 1.0 / nt
+        grid = W.Grid(model.shape, model.spacing, model.origin, k, dt, nt)
+        ctx = W.Context(0)
+        m = torch.from_numpy(model.m32()).cuda()
+        eta = torch.from_numpy(model.eta32()).cuda()
+        q = torch.from_numpy(model.wavelet(dt, nt)).cuda()
+        d = torch.zeros((nt, len(model.rec)), device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        W.wp_forward_dev(ctx.handle, grid, m, eta, q, model.src, model.rec, d)
+        torch.cuda.synchronize()
+        e0.record()
+        W.wp_forward_dev(ctx.handle, grid, m, eta, q, model.src, model.rec, d)
+        e1.record()
+        torch.cuda.synchronize()
+        s = e0.elapsed_time(e1) * 1e-3
+        npts = int(np.prod(model.shape))
+        out.append({"grid": list(model.shape), "space_order": k, "modelled_s": 1.0, "nt": nt, "dt_s": dt,
+                    "time_to_solution_s": s, "gpts_per_s": npts * nt / s / 1e9,
+                    "paper_time_to_solution_s": PAPER_TIME_TO_SOLUTION_S.get(n),
+                    "paper_hardware": "Intel Skylake 8180, 28 cores, 2.5 GHz (CPU; dt and model not stated)"})
+        ctx.close()
+        del m, eta, q, d
+        torch.cuda.empty_cache()
+    return out
+
+
 def cfd_leg(args):
     """The CFD examples of Sec. 5 at GPU scale: 8192^2 fields (67 M points, 256 MB
     each, larger than L2), convection and Poisson 200 steps, Burgers' equation 100,
@@ -628,6 +684,10 @@ def run_ours(args):
     if args.cfd_n > 0 and world == 1:
         cfd = cfd_leg(args)
 
+    context = None
+    if args.context and world == 1:
+        context = paper_context_leg(args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, steps, el, nthreads = oracle_sample(model, dt, args.cpu_seconds)
@@ -639,7 +699,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": describe(model, nt, dt),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clk.summary(), "gradient": gradient, "serving": serving, "large": large, "cfd": cfd}
+                "clocks": clk.summary(), "gradient": gradient, "serving": serving, "large": large, "cfd": cfd, "paper_context": context}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
