@@ -29,6 +29,9 @@ MUTANTS = {
     "interp_fraction_flipped": ("frac[d] = t - double(i);", "frac[d] = 1.0 - (t - double(i));"),
     "centre_counted_twice": ("T s = alpha[0] * uc;", "T s = 2.0 * alpha[0] * uc;"),
     "previous_level_sign": ("mm * (2.0 * un - um)", "mm * (2.0 * un + um)"),
+    "cfl_signed_weight_sum": ("A += 2.0 * std::fabs(alpha[j]);", "A += 2.0 * alpha[j];"),
+    "cfl_missing_sqrt": ("*dt_max = 2.0 / (vmax * std::sqrt(s));", "*dt_max = 2.0 / (vmax * s);"),
+    "checkpoint_pair_off_by_one": ("ck_prev.push_back(*uprev);", "ck_prev.push_back(*u);"),
 }
 
 
@@ -42,6 +45,8 @@ def _pins():
         "dot": lambda: P.test_dot_test_2d(4),
         "interp": lambda: P.test_interpolation_invariants((9, 11)),
         "complex_step": lambda: P.test_gradient_matches_complex_step((9, 10), 4),
+        "cfl": lambda: P.test_cfl_bound_matches_symbol_maximum(8, 6.502),
+        "checkpoint_interval": P.test_gradient_independent_of_checkpoint_interval,
     }
     failed = []
     for name, fn in checks.items():
