@@ -55,8 +55,12 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--serving", type=int, default=24,
+    p.add_argument("--serving", type=int, default=256,
                    help="requests of the shot-serving stream (0 skips the serving leg)")
+    p.add_argument("--serving-calibration", type=int, default=24,
+                   help="requests timed one by one to set the arrival rate (1.25x their service rate)")
+    p.add_argument("--serving-capacity", action="store_true",
+                   help="also serve the whole stream queued at t = 0 (served and plain)")
     p.add_argument("--serving-slots", type=int, default=4)
     p.add_argument("--serving-scale", type=float, default=1.0,
                    help="scale of the request sizes and nt (1.0 = 128..320 x 128..320 x 128..200 + 40, nt 500..2000)")
@@ -77,6 +81,9 @@ def parse():
                    help="skip the full-history gradient (snap_interval 1, ~135 GB) timed beside the snapshot one")
     p.add_argument("--no-reconstruct", dest="reconstruct", action="store_false",
                    help="skip the boundary-reconstruction gradient timed beside the snapshot one")
+    p.add_argument("--orders", type=lambda v: [int(x) for x in v.split(",") if x.strip() and int(x) > 0],
+                   default=[4, 8, 12, 16], help="space orders of the roofline sweep ('0' skips it)")
+    p.add_argument("--order-shots", type=int, default=3, help="timed shots per order of the roofline sweep")
     p.add_argument("--profile-every", type=int, default=10,
                    help="bracket every N-th stencil launch with CUDA events in the timed region")
     return p.parse_args()
@@ -219,14 +226,15 @@ def kernel_traffic(space_order, grid):
     path = os.path.join(ROOT, "profiles", f"stencil3d_fwd_so{space_order}_{grid}.md")
     if not os.path.exists(path):
         return None
-    src = open(os.path.join(ROOT, "paper_1808_01995_gb300", "csrc", "stencil3d.cuh"), "rb").read()
+    name = "stencil3d.cuh" if space_order <= 8 else "stencil3d_hi.cuh"
+    src = open(os.path.join(ROOT, "paper_1808_01995_gb300", "csrc", name), "rb").read()
     sha = hashlib.sha256(src).hexdigest()[:16]
     vals = {}
     for line in open(path):
         if ": " in line and line.startswith("- "):
             k, v = line[2:].split(": ", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("stencil3d.cuh sha256[:16]") != sha:
+    if vals.get(f"{name} sha256[:16]") != sha:
         return None
     try:
         return float(vals["dram bytes per launch"])
@@ -237,23 +245,34 @@ def kernel_traffic(space_order, grid):
 # ---------------------------------------------------------------------------
 # oracle legs (CPU)
 # ---------------------------------------------------------------------------
+def oracle_timed(model, dt, steps):
+    """Seconds of one FP64 oracle forward of `steps` time steps on the full grid
+    (the call allocates and zeroes its FP64 fields first)."""
+    import oracle as O
+    g = O.Grid(model.shape, model.spacing, model.origin, model.space_order, dt, steps)
+    q = model.wavelet(dt, steps)
+    m, eta = model.m32(), model.eta32()
+    t0 = time.perf_counter()
+    O.forward(g, m, eta, q, model.src, model.rec)
+    return time.perf_counter() - t0
+
+
 def oracle_sample(model, dt, budget_s):
-    """Time the FP64 oracle's forward on the same grid for a bounded number of time
-    steps; returns (Gpts/s, steps, seconds, threads)."""
+    """The FP64 oracle's forward rate on the full grid over a bounded number of time
+    steps: the steps are grown until one run takes about budget_s / 2, and the rate
+    is taken from the difference with a one-step run, so that the per-call setup
+    (allocating and zeroing the FP64 fields) cancels.
+    Returns (Gpts/s, steps, seconds of the longest run, threads)."""
     import oracle as O
     nthreads = O.num_threads()
-    k = model.space_order
-    steps = 1
+    t1 = oracle_timed(model, dt, 1)
+    steps = 2
     while True:
-        g = O.Grid(model.shape, model.spacing, model.origin, k, dt, steps)
-        q = model.wavelet(dt, steps)
-        t0 = time.perf_counter()
-        O.forward(g, model.m32(), model.eta32(), q, model.src, model.rec)
-        el = time.perf_counter() - t0
+        el = oracle_timed(model, dt, steps)
         if el >= 0.5 * budget_s or steps >= 4096:
             break
-        steps = max(steps + 1, min(steps * 8, int(steps * 0.6 * budget_s / max(el, 1e-3))))
-    return np.prod(model.shape) * steps / el / 1e9, steps, el, nthreads
+        steps = max(steps + 1, min(steps * 8, int(steps * 0.6 * budget_s / max(el - t1, 1e-3))))
+    return np.prod(model.shape) * (steps - 1) / max(el - t1, 1e-9) / 1e9, steps, el, nthreads
 
 
 def oracle_sample_one_thread(model, dt, nthreads, budget_s=2.0):
@@ -269,28 +288,39 @@ def oracle_sample_one_thread(model, dt, nthreads, budget_s=2.0):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores.  One bench step is a
+    bounded sample of the shot (n of its time steps, n fixed in the warm-up so the
+    whole run stays within about --cpu-seconds); ms_per_step is the time of that
+    sample as run, and the rate (value) is taken from the difference with a
+    one-step run, so that the oracle's per-call setup cancels."""
     world, rank, local = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
     if rank != 0:
         return
     from paper_1808_01995_gb300 import synth  # noqa: F401  (inputs only)
     import oracle as O
+    t_start = time.perf_counter()
     model = workload(args)
     dt = 0.9 * O.cfl_dt(model.spacing, args.space_order, model.vmax)
-    per_step = max(1.0, args.cpu_seconds / max(args.steps, 1))
-    vals = []
     nthreads = O.num_threads()
-    steps_used = 0
-    for i in range(args.warmup + args.steps):
-        rate, steps, el, nthreads = oracle_sample(model, dt, per_step if i >= args.warmup else 0.5)
-        if i >= args.warmup:
-            vals.append(rate)
-            steps_used = steps
-    v = float(np.median(vals))
-    sample = (f"FP64 oracle forward on the full {model.shape} grid for {steps_used} of {args.nt} time steps "
-              f"per step (rate scales linearly in steps)")
+    npts = int(np.prod(model.shape))
+    # warm-up: the one-step time (setup + 1 step) and the sample length
+    t1 = min(oracle_timed(model, dt, 1) for _ in range(max(args.warmup, 1)))
+    per_step_s = max(0.5, args.cpu_seconds / max(args.steps, 1))
+    t_probe = oracle_timed(model, dt, 4)
+    step_s = max((t_probe - t1) / 3, 1e-4)
+    n = int(max(2, min(args.nt, 1 + (per_step_s - t1) / step_s)))
+    times = [oracle_timed(model, dt, n) for _ in range(args.steps)]
+    t_med = float(np.median(times))
+    v = npts * (n - 1) / max(t_med - t1, 1e-9) / 1e9
+    timed_s = float(sum(times))
+    sample = (f"FP64 oracle forward on the full {model.shape} grid, {n} of the shot's {args.nt} time steps "
+              f"per bench step; rate from the difference with a one-step run ({t1:.2f} s, the setup)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gpts/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": np.prod(model.shape) * args.nt / (v * 1e9) * 1e3, "higher_is_better": True,
+            "ms_per_step": t_med * 1e3, "ms_per_step_is": f"one bench step = {n} oracle time steps, as run",
+            "ms_per_shot_extrapolated": npts * args.nt / (v * 1e9) * 1e3,
+            "seconds_timed": timed_s, "seconds_total": time.perf_counter() - t_start,
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": describe(model, args.nt, dt),
             "cpu_baseline": {"value": v, "unit": "Gpts/s", "cores": nthreads, "kind": "oracle", "sample": sample},
@@ -302,13 +332,17 @@ def run_reference(args):
 # our arm
 # ---------------------------------------------------------------------------
 def serving_leg(args):
-    """Shot-serving stream: Poisson arrivals at 1.25x the sequential service rate,
-    served by ShotServer (continuous batching) and, for comparison, one request
-    at a time with a fresh context each (plain calls)."""
+    """Shot-serving stream (the 256-request Poisson stream by default): arrivals at
+    1.25x the plain sequential service rate (estimated on the first requests), served by
+    ShotServer (continuous batching) and, for comparison, one request at a time
+    with a fresh context each (plain calls) and one request at a time on one
+    reused context (no overlap, but nothing re-created: what the server gains
+    beyond that is the overlap)."""
     from concurrent.futures import ThreadPoolExecutor
 
     from paper_1808_01995_gb300 import serving as S
     from paper_1808_01995_gb300 import synth
+    from paper_1808_01995_gb300 import wavprop as W
     specs = synth.serving_requests(count=args.serving, size_scale=args.serving_scale)
     with ThreadPoolExecutor(8) as ex:
         base = list(ex.map(S.make_request, specs))
@@ -321,11 +355,12 @@ def serving_leg(args):
             out.append(c)
         return out
 
-    # calibration: sequential service times (also warms the caches)
+    # calibration: plain sequential service times (fresh context per request) of a
+    # sample of the stream; also warms the host caches
     import time as _t
-    from paper_1808_01995_gb300 import wavprop as W
+    ncal = min(len(base), args.serving_calibration)
     service = []
-    for r in fresh():
+    for r in fresh()[:ncal]:
         t0 = _t.perf_counter()
         with W.Context(0) as c:
             S.run_request(c.handle, r)
@@ -333,28 +368,52 @@ def serving_leg(args):
     mu = 1.0 / float(np.mean(service))
     rate = 1.25 * mu
     arrivals = S.poisson_arrivals(len(base), rate, seed=1808 + 4)
-    plain = S.serve_sequential_plain(fresh(), arrivals)
     served = S.serve_stream(fresh(), arrivals, slots=args.serving_slots)
-    # capacity: the whole stream queued at t = 0
-    burst = np.zeros(len(base))
-    plain_sat = S.serve_sequential_plain(fresh(), burst)
-    served_sat = S.serve_stream(fresh(), burst, slots=args.serving_slots)
+    plain = S.serve_sequential_plain(fresh(), arrivals)
+    reused = S.serve_sequential_plain(fresh(), arrivals, reuse_context=True)
     kinds = [s["kind"] for s in specs]
-    return {"requests": len(base), "forward": kinds.count("forward"), "gradient": kinds.count("gradient"),
-            "arrival_rate_per_s": rate, "sequential_service_rate_per_s": mu,
-            "mean_service_s": float(np.mean(service)),
-            "size_scale": args.serving_scale,
-            "served": served, "plain": plain,
-            "p99_speedup": (plain["p99_latency_s"] / served["p99_latency_s"]
-                            if served["p99_latency_s"] else None),
-            "shots_per_hour_ratio": (served["shots_per_hour"] / plain["shots_per_hour"]
-                                     if plain["shots_per_hour"] else None),
-            "capacity": {"served_shots_per_hour": served_sat["shots_per_hour"],
-                         "plain_shots_per_hour": plain_sat["shots_per_hour"],
-                         "served_p99_s": served_sat["p99_latency_s"], "plain_p99_s": plain_sat["p99_latency_s"],
-                         "served_errors": served_sat["errors"], "plain_errors": plain_sat["errors"],
-                         "ratio": (served_sat["shots_per_hour"] / plain_sat["shots_per_hour"]
-                                   if plain_sat["shots_per_hour"] else None)}}
+
+    def ratio(a, b):
+        return a / b if a and b else None
+
+    out = {"requests": len(base), "forward": kinds.count("forward"), "gradient": kinds.count("gradient"),
+           "arrival_rate_per_s": rate, "sequential_service_rate_per_s": mu,
+           "mean_service_s": float(np.mean(service)), "calibration_requests": ncal,
+           "size_scale": args.serving_scale,
+           "served": served, "plain": plain, "plain_reused_context": reused,
+           "p99_speedup": ratio(plain["p99_latency_s"], served["p99_latency_s"]),
+           "shots_per_hour_ratio": ratio(served["shots_per_hour"], plain["shots_per_hour"]),
+           "vs_reused_context": {"p99_speedup": ratio(reused["p99_latency_s"], served["p99_latency_s"]),
+                                 "shots_per_hour_ratio": ratio(served["shots_per_hour"], reused["shots_per_hour"])}}
+    if args.serving_capacity:
+        # capacity: the whole stream queued at t = 0
+        burst = np.zeros(len(base))
+        plain_sat = S.serve_sequential_plain(fresh(), burst)
+        served_sat = S.serve_stream(fresh(), burst, slots=args.serving_slots)
+        out["capacity"] = {"served_shots_per_hour": served_sat["shots_per_hour"],
+                           "plain_shots_per_hour": plain_sat["shots_per_hour"],
+                           "served_p99_s": served_sat["p99_latency_s"], "plain_p99_s": plain_sat["p99_latency_s"],
+                           "served_errors": served_sat["errors"], "plain_errors": plain_sat["errors"],
+                           "ratio": ratio(served_sat["shots_per_hour"], plain_sat["shots_per_hour"])}
+    return out
+
+
+def gradient_alg_bytes(npts, ndamp, nt, nseg):
+    """Compulsory HBM bytes of the snapshot gradient (forward with snapshot pairs,
+    recompute between them, adjoint with the fused correlation): per time step the
+    forward and the recomputed stencil each move 16 B/pt (u^n, u^{n-1}, b read,
+    u^{n+1} written) + 4 B/pt where damped (s), the adjoint+gradient stencil the same
+    plus 4 B/pt (u^j) and 8 B/pt (gradient read and written); each snapshot pair
+    writes 8 B/pt; the gradient is zeroed and copied out once (12 B/pt)."""
+    stencil = 16 * npts + 4 * ndamp
+    return nt * (2 * stencil + stencil + 12 * npts) + nseg * 8 * npts + 12 * npts
+
+
+def full_history_alg_bytes(npts, ndamp, nt):
+    """The same for the whole-history gradient: the forward stencil's output is the
+    stored level (no snapshot copies, no recompute)."""
+    stencil = 16 * npts + 4 * ndamp
+    return nt * (stencil + stencil + 12 * npts) + 12 * npts
 
 
 def gradient_leg(args):
@@ -387,6 +446,8 @@ def gradient_leg(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.gradient
     npts = int(np.prod(true.shape))
+    ndamp = int(np.count_nonzero(true.eta))
+    nseg = -(-nt // S)
     peak = W.wp_bytes_in_use(ctx.handle)
     # the same gradient with binomial checkpointing (given residual, own context for its memory)
     d0 = torch.zeros_like(d_obs)
@@ -438,10 +499,25 @@ def gradient_leg(args):
         rc = {"ms_per_gradient": e0.elapsed_time(e1), "device_bytes": int(W.wp_bytes_in_use(rctx.handle)),
               "rel_l2_vs_snapshots_interior": float((a - b).norm() / b.norm())}
         rctx.close()
+    hbm, hbm_kind = measured_peaks()
+    alg = gradient_alg_bytes(npts, ndamp, nt, nseg)
+    roof = {"bound": "hbm", "alg_bytes": alg, "bytes_per_point_step": alg / (npts * nt),
+            "achieved": alg / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": alg / (ms * 1e-3) / 1e9 / hbm, "peak_source": hbm_kind,
+            "counted": "per step: forward stencil 16 B/pt + 4 B/pt damped, recompute the same, adjoint stencil "
+                       "the same + u^j read 4 B/pt + gradient read-modify-write 8 B/pt; 8 B/pt per snapshot pair; "
+                       "12 B/pt once (gradient zeroed, copied out)"}
+    if fh:
+        alg_fh = full_history_alg_bytes(npts, ndamp, nt)
+        fh["roofline"] = {"alg_bytes": alg_fh, "achieved": alg_fh / (fh["ms_per_gradient"] * 1e-3) / 1e9,
+                          "frac": alg_fh / (fh["ms_per_gradient"] * 1e-3) / 1e9 / hbm, "peak": hbm,
+                          "counted": "forward stencil (its output is the stored level) + adjoint stencil with "
+                                     "u^j read and gradient read-modify-write, per step"}
     return {"workload": f"blobs3d 200^3 + 40 ({true.shape[0]}^3) SO8, nt={nt}, snapshots every {S}, "
                         f"{len(true.rec)} receivers", "ms_per_gradient": ms,
             "gpts_per_s": npts * nt / (ms * 1e-3) / 1e9, "misfit": J, "device_bytes": int(peak),
             "passes": "forward with snapshots + recompute + adjoint with fused correlation",
+            "roofline": roof,
             "full_history": fh, "binomial_checkpointing": ck, "boundary_reconstruction": rc}
 
 
@@ -539,6 +615,56 @@ def paper_context_leg(args):
                     "paper_hardware": "Intel Skylake 8180, 28 cores, 2.5 GHz (CPU; dt and model not stated)"})
         ctx.close()
         del m, eta, q, d
+        torch.cuda.empty_cache()
+    return out
+
+
+def order_sweep_leg(args, headline):
+    """The stencil sweep workload (256^3 + 40-point layer, 1000 steps) at each space
+    order of --orders: the shot's rate and the stencil kernel's compulsory bytes
+    over its CUDA-event average (every launch bracketed), against the measured HBM
+    copy bandwidth.  The headline order reuses the headline run."""
+    import torch
+    from paper_1808_01995_gb300 import wavprop as W
+    peak, peak_kind = measured_peaks()
+    out = {}
+    for k in args.orders:
+        if k == args.space_order and headline is not None:
+            out[f"so{k}"] = headline
+            continue
+        args_k = argparse.Namespace(**vars(args))
+        args_k.space_order = k
+        model = workload(args_k)
+        dt = 0.9 * W.wp_cfl_dt(W.Grid(model.shape, model.spacing, model.origin, k), model.vmax)
+        nt = args.nt
+        grid = W.Grid(model.shape, model.spacing, model.origin, k, dt, nt)
+        with W.Context(0) as ctx:
+            m = torch.from_numpy(model.m32()).cuda()
+            eta = torch.from_numpy(model.eta32()).cuda()
+            q = torch.from_numpy(model.wavelet(dt, nt)).cuda()
+            rec = torch.zeros((nt, len(model.rec)), device="cuda")
+            W.wp_forward_dev(ctx.handle, grid, m, eta, q, model.src, model.rec, rec)
+            torch.cuda.synchronize()
+            W.wp_set_profiling(ctx.handle, 1)
+            W.wp_profile_read(ctx.handle, reset=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.order_shots):
+                W.wp_forward_dev(ctx.handle, grid, m, eta, q, model.src, model.rec, rec)
+            e1.record()
+            torch.cuda.synchronize()
+            k_ms, k_n = W.wp_profile_read(ctx.handle, reset=True)
+            ms = e0.elapsed_time(e1) / args.order_shots
+        alg, npts, _ = algorithmic_bytes_per_launch(model)
+        avg_s = k_ms / max(k_n, 1) * 1e-3
+        out[f"so{k}"] = {"value": npts * nt / (ms * 1e-3) / 1e9, "unit": "Gpts/s", "ms_per_shot": ms,
+                         "kernel": f"{'stencil3d_kernel' if k <= 8 else 'stencil3d_hi_kernel'}<R={k // 2},fwd>",
+                         "kernel_avg_us": avg_s * 1e6, "alg_bytes_per_launch": alg,
+                         "achieved": alg / avg_s / 1e9, "peak": peak, "unit_roofline": "GB/s",
+                         "frac": alg / avg_s / 1e9 / peak, "peak_source": peak_kind,
+                         "traffic": kernel_traffic(k, "x".join(str(s) for s in model.shape)),
+                         "timed_launches": k_n}
+        del m, eta, q, rec
         torch.cuda.empty_cache()
     return out
 
@@ -644,7 +770,8 @@ def run_ours(args):
     achieved = alg_bytes / k_avg_s / 1e9
     traffic = kernel_traffic(k, "x".join(str(s) for s in model.shape))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": f"stencil3d_kernel<R={k // 2},fwd>",
+                "traffic": traffic,
+                "kernel": f"{'stencil3d_kernel' if k <= 8 else 'stencil3d_hi_kernel'}<R={k // 2},fwd>",
                 "kernel_avg_us": k_avg_s * 1e6, "alg_bytes_per_launch": alg_bytes,
                 "timed_launches": k_n, "sampled_every": args.profile_every,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
@@ -670,7 +797,7 @@ def run_ours(args):
 
         e2e_step()
         torch.cuda.synchronize()
-        ke = max(1, min(args.steps, 3))
+        ke = max(1, args.steps)
         barrier(world)
         t0 = time.perf_counter()
         for _ in range(ke):
@@ -683,6 +810,15 @@ def run_ours(args):
                "call": "wp_forward (host arrays, pinned)"}
 
     # single-GPU legs: reported by the N = 1 run (replicas add nothing to them)
+    by_order = None
+    if args.orders and world == 1:
+        head = {"value": value, "unit": "Gpts/s", "ms_per_shot": ms / args.steps, "kernel": roofline["kernel"],
+                "kernel_avg_us": roofline["kernel_avg_us"], "alg_bytes_per_launch": alg_bytes,
+                "achieved": achieved, "peak": peak, "unit_roofline": "GB/s", "frac": achieved / peak,
+                "peak_source": peak_kind, "traffic": traffic, "timed_launches": k_n,
+                "note": "the headline run (launches sampled every --profile-every)"}
+        by_order = order_sweep_leg(args, head)
+
     gradient = None
     if args.gradient > 0 and world == 1:
         gradient = gradient_leg(args)
@@ -718,7 +854,7 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": describe(model, nt, dt),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "value_interior": interior,
-                "clocks": clk.summary(), "gradient": gradient, "serving": serving, "large": large, "cfd": cfd, "paper_context": context}
+                "clocks": clk.summary(), "roofline_by_order": by_order, "gradient": gradient, "serving": serving, "large": large, "cfd": cfd, "paper_context": context}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

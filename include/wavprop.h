@@ -85,7 +85,11 @@ void wp_destroy(wp_ctx *ctx);
 const char *wp_last_error(void);
 
 /* Seconds after which a call gives up waiting for its device work and returns
- * WP_ETIMEOUT (default 600).  The context must not be reused after a timeout. */
+ * WP_ETIMEOUT (default 600).  The context must not be reused after a timeout
+ * (every later call on it returns WP_ETIMEOUT).  The work it had queued keeps
+ * running and may still write the call's output arrays: synchronise the device
+ * (cudaDeviceSynchronize) before reading, reusing or freeing them, and before
+ * wp_destroy. */
 int wp_set_timeout(wp_ctx *ctx, double seconds);
 
 /* Weights a_0..a_{k/2} of the order-k central second derivative
@@ -101,8 +105,7 @@ int wp_cfl_dt(const wp_grid *grid, double vmax, double *dt_max);
 /* Device bytes a call would hold for this grid: mode 0 forward/adjoint,
  * 1 gradient with the given snapshot interval, 2 checkpointed gradient with
  * snap_interval stored states, 3 gradient by boundary reconstruction (an upper
- * bound; snap_interval unused).  Temporal blocking (wp_set_temporal_blocking)
- * adds two fields to mode 0. */
+ * bound; snap_interval unused). */
 int wp_estimate_bytes(const wp_grid *grid, int nsrc, int nrec, int mode, int snap_interval,
                       size_t *bytes);
 
@@ -176,7 +179,10 @@ int wp_checkpoint_schedule(int nt, int checkpoints, int *ops, int max_ops, int *
  * Same contracts; m, eta, wavelet, rec/src data and outputs are device pointers
  * (contiguous, float), coordinates stay on the host.  Work is ordered after
  * everything already queued on `stream` (a cudaStream_t, NULL = legacy default
- * stream), and later work on `stream` is ordered after it. */
+ * stream), and later work on `stream` is ordered after it.  Every device-array
+ * argument (and those of the CFD, axpy and model-update _dev calls) must be
+ * device or managed memory of the context's device: a host pointer or memory of
+ * another GPU is refused with WP_EINVAL before anything is launched. */
 int wp_forward_dev(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *eta,
                    const float *wavelet, int nsrc, const double *src_coords, int nrec,
                    const double *rec_coords, float *rec_out, void *stream);
@@ -221,6 +227,13 @@ int wp_fwi_gradient_dev(wp_ctx *ctx, const wp_grid *grid, const float *m, const 
  *   wp_update_model_dev: m[i] = min(max(m[i] - step grad[i], m_min), m_max),
  *                        with 0 < m_min <= m_max (squared-slowness bounds). */
 int wp_axpy_dev(wp_ctx *ctx, long long n, float alpha, const float *x, float *y, void *stream);
+
+/* Misfit of one shot (Eq. AS): r_out[i] = d[i] - d_obs[i] for i < n and
+ * *misfit = 1/2 sum r_i^2, summed in double in a fixed order (the same kernel and
+ * order as wp_fwi_gradient's misfit, so the two agree bitwise).  Device arrays;
+ * WP_ENONFINITE if the sum is not finite. */
+int wp_misfit_dev(wp_ctx *ctx, long long n, const float *d, const float *d_obs, float *r_out,
+                  double *misfit, void *stream);
 int wp_update_model_dev(wp_ctx *ctx, long long n, float step, const float *grad, float *m,
                         float m_min, float m_max, void *stream);
 
@@ -247,16 +260,13 @@ int wp_forward_save(wp_ctx *ctx, const wp_grid *grid, const float *m, const floa
 int wp_backward(wp_state *state, const float *residual, float *grad_out, void *stream);
 void wp_state_free(wp_state *state);
 
-/* Temporal blocking of forward (and few-receiver adjoint) time loops of 3D grids
- * with space order <= 8 and at most 64 injection targets; results are identical
- * in every mode.  mode 0: one stencil launch per time step (default); 1: two
- * steps per launch, u^{n+1} kept on chip with the rim computed twice; 2: two steps
- * per launch by two roles of CTAs (one cooperative launch, one grid column per
- * CTA; u^{n+1} read back from L2), used when twice the columns fit on the GPU at
- * once.  Both need two extra wavefields.  The initial mode comes from
- * WP_TEMPORAL_BLOCKING when the context is created.  No counterpart in the paper,
- * which blocks loops in space only. */
-int wp_set_temporal_blocking(wp_ctx *ctx, int mode);
+/* Limit, in seconds, of every wait inside the context's stencil kernels (a
+ * kernel waits for its own TMA copies and ring slots; default 2 s, at most 60).
+ * A wait that runs out makes the kernel skip its remaining stores and the call
+ * return WP_EDEVICE; the context stays usable (set a larger limit and call
+ * again).  0 means that any wait which is not already complete at its first look
+ * gives up at once: it exists to exercise that error path. */
+int wp_set_wait_limit(wp_ctx *ctx, double seconds);
 
 /* ---- The computational-fluid-dynamics examples of Sec. 5 (2D, FP32) --------
  * Fields are (ny, nx) arrays in C order (x fastest).  Each call advances the
@@ -320,8 +330,11 @@ int wp_profile_read(wp_ctx *ctx, double *stencil_ms, uint64_t *stencil_launches,
  *     (the call clears what must start at zero).  Calls that overlap on the GPU,
  *     from several streams or host threads, race on it and corrupt each other's
  *     results: serialise them.
- * Work runs on `stream` (NULL = legacy default stream) and the call returns
- * after it has finished. */
+ * Work runs on the current device, on `stream` (NULL = legacy default stream),
+ * and the call returns after it has finished.  m, eta, wavelet and rec_out must
+ * be device memory of the current device and `stream` must belong to it, else
+ * WP_EINVAL (nothing launched).  After an error the call also waits for any
+ * work it had already queued, so the array is idle when it returns. */
 #define WP_NOALLOC_MAX_BYTES ((size_t)64 << 20)
 int wp_forward_noalloc(const wp_grid *grid, const float *m, const float *eta,
                        const float *wavelet, int nsrc, const double *src_coords, int nrec,

@@ -9,10 +9,11 @@ snapshots), and into dL/dq = F^T (dL/dd) with the adjoint propagator (Eq. Adj)
 when the wavelet requires a gradient.  eta (the absorbing-layer profile) is an
 input of the operator, not a parameter: it receives no gradient.
 
-``misfit`` is J = 1/2 ||d - d_obs||^2, whose gradient with respect to d is the
-residual d - d_obs, so ``misfit(prop(m), d_obs).backward()`` yields dJ/dm.
-All arithmetic runs in the CUDA library; torch provides device memory, streams
-and the autograd graph.
+``misfit`` is J = 1/2 ||d - d_obs||^2 (the library's residual kernel), whose
+gradient with respect to d is the residual d - d_obs, so
+``misfit(prop(m), d_obs).backward()`` yields dJ/dm.  The propagator's arithmetic
+runs in the CUDA library; torch provides device memory, streams and the autograd
+graph (and scales the residual by the upstream gradient of J, a scalar).
 """
 from __future__ import annotations
 
@@ -45,6 +46,7 @@ class AcousticForward(torch.autograd.Function):
     @staticmethod
     def forward(ctx, m, eta, wavelet, prop):
         grid = prop.grid
+        m, eta, wavelet = m.contiguous(), eta.contiguous(), wavelet.contiguous()
         d = torch.empty((grid.nt, len(prop.rec)), device=m.device, dtype=torch.float32)
         ctx.prop = prop
         ctx.save_for_backward(m, eta)
@@ -96,7 +98,39 @@ class AcousticPropagator:
         return AcousticForward.apply(m, eta, wavelet, self)
 
 
+_misfit_contexts: dict = {}
+
+
+def _misfit_context(device) -> W.Context:
+    """One small library context per device for the misfit kernel (created on first use)."""
+    idx = device.index if device.index is not None else torch.cuda.current_device()
+    c = _misfit_contexts.get(idx)
+    if c is None:
+        c = _misfit_contexts[idx] = W.Context(idx)
+    return c
+
+
+class Misfit(torch.autograd.Function):
+    """J = 1/2 ||d - d_obs||^2 (Eq. AS) by the library's residual kernel (r = d - d_obs
+    and the sum of r^2 in double, fixed order); dJ/dd = r, dJ/dd_obs = -r."""
+
+    @staticmethod
+    def forward(ctx, d, d_obs):
+        d = d.detach().contiguous()
+        d_obs = d_obs.detach().contiguous()
+        r = torch.empty_like(d)
+        J = W.wp_misfit_dev(_misfit_context(d.device).handle, d, d_obs, r)
+        ctx.save_for_backward(r)
+        return torch.tensor(J, dtype=torch.float64, device=d.device)
+
+    @staticmethod
+    def backward(ctx, g):
+        (r,) = ctx.saved_tensors
+        gr = (r * g.to(r.dtype)) if g is not None else r
+        return gr, -gr
+
+
 def misfit(d, d_obs):
-    """J = 1/2 ||d - d_obs||^2 (Eq. AS)."""
-    r = d - d_obs
-    return 0.5 * (r * r).sum()
+    """J = 1/2 ||d - d_obs||^2 (Eq. AS) as a float64 scalar tensor; differentiable in d
+    (and d_obs)."""
+    return Misfit.apply(d, d_obs)

@@ -3,6 +3,7 @@
 // the time loops (forward, adjoint, forward with snapshots, backward with
 // recompute + fused gradient), and the C ABI declared in wavprop.h.
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -22,7 +23,7 @@
 #include "../../include/wavprop.h"
 #include "kernels.cuh"
 #include "stencil3d.cuh"
-#include "stencil3d_tb.cuh"
+#include "stencil3d_hi.cuh"
 
 using namespace wp;
 
@@ -53,6 +54,15 @@ static int fail(int code, const char *fmt, ...) {
     if (rc_ != WP_OK) return rc_; \
   } while (0)
 
+// NVTX range over a host scope (the phases of a call: forward, adjoint,
+// recompute, ...); free when no profiler is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 // ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
@@ -72,9 +82,7 @@ struct wp_ctx {
   int smem3d[2][9] = {};
   int occ3d[2][9] = {};
   int ty3d[2][9] = {};
-  int smem_tb[5] = {}, occ_tb[5] = {};     // two-step kernel, half-orders 1..4
-  int smem_pair[5] = {}, occ_pair[5] = {}; // two-role (pair) kernel, half-orders 1..4
-  int temporal_blocking = 0;              // 0 single steps; 1 two-step kernel; 2 CTA pairs
+  uint64_t wait_ns = kWaitLimitNs;        // limit of the kernels' ring waits
   bool broken = false;
   // profiling: an event pair around every prof_every-th stencil launch, summed on read
   bool profiling = false;
@@ -209,11 +217,21 @@ static int ctx_wait(wp_ctx *c, const char *what = "device work") {
   return WP_OK;
 }
 
+static const char *device_error_text(int code) {
+  switch (code) {
+    case kErrWaitFull: return "a wait inside a kernel gave up (its limit ran out)";
+    case kErrLaunch: return "a kernel was launched with an unsupported shape";
+    case kErrBounds: return "a bounds check failed (debug build)";
+    default: return "unknown device error";
+  }
+}
+
 static int check_device_error(wp_ctx *c) {
   CU(cudaMemcpyAsync(c->h_scalars, c->d_scalars, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   TRY(ctx_wait(c));
   if (c->h_scalars[0] != 0)
-    return fail(WP_EDEVICE, "a kernel reported device error %d (a wait timed out)", c->h_scalars[0]);
+    return fail(WP_EDEVICE, "a kernel reported device error %d: %s", c->h_scalars[0],
+                device_error_text(c->h_scalars[0]));
   return WP_OK;
 }
 
@@ -336,6 +354,12 @@ static LapCoef lap_coef(const Geom &G) {
     c.cz[j] = static_cast<float>(a[j] * iz);
     c.cy[j] = static_cast<float>(a[j] * iy);
     c.cx[j] = static_cast<float>(a[j] * ix);
+  }
+  c.p0 = make_float2(c.c0, c.c0);
+  for (int j = 0; j < 9; ++j) {
+    c.pz[j] = make_float2(c.cz[j], c.cz[j]);
+    c.py[j] = make_float2(c.cy[j], c.cy[j]);
+    c.px[j] = make_float2(c.cx[j], c.cx[j]);
   }
   return c;
 }
@@ -483,8 +507,6 @@ struct Field3 {
   float *p = nullptr;
   bool mapped = false;  // descriptors encoded for p
   CUtensorMap halo[2], tile[2];
-  bool tb_mapped = false;  // two-step kernel: [0] u^n plane box, [1] region box, [2] core box
-  CUtensorMap tb[3];
 };
 
 static int make_field_maps(Field3 *f, const Geom &G) {
@@ -495,13 +517,6 @@ static int make_field_maps(Field3 *f, const Geom &G) {
     TRY(make_map(&f->tile[mode], f->p, G, tx, ty));
   }
   f->mapped = true;
-  TbShape sh;
-  if (stencil3d_tb_shape(G.R, &sh)) {
-    TRY(make_map(&f->tb[0], f->p, G, sh.plane_w, sh.plane_h));
-    TRY(make_map(&f->tb[1], f->p, G, sh.region_w, sh.region_h));
-    TRY(make_map(&f->tb[2], f->p, G, sh.core_w, sh.core_h));
-    f->tb_mapped = true;
-  }
   return WP_OK;
 }
 
@@ -569,12 +584,6 @@ struct Prop {
   bool sub = false;  // a sub-box for prop_step(..., sub = true): box (x0 a multiple of 4) and its plans
   Box box;
   Plan3d plan_sub[2];
-  bool tb = false;  // the two-step kernel covers this grid
-  Plan3d plan_tb;
-  bool pair = false;  // the two-role kernel covers this grid: one column per CTA, all resident
-  Plan3d plan_pair;
-  unsigned *progress = nullptr;  // [column] planes of u^{n+1} published
-  uint2 *tb_bits = nullptr;  // [tile][nzw] damping words of the two-step tiles
 };
 
 // dt, dt^2 and dt/2 for the coefficient kernel, each as a float pair hi + lo
@@ -637,45 +646,6 @@ static int prop_setup(wp_ctx *c, Arena &ar, const Geom &G, const float *m, const
     TRY(make_field_maps(&P->b, G));
     TRY(make_field_maps(&P->s, G));
     for (int mode = 0; mode < 2; ++mode) P->plan[mode] = plan3d(G, mode, c->num_sms, c->occ3d[mode][G.R]);
-    if (G.R <= 4 && c->occ_pair[G.R] > 0) {
-      // the single-step plan's items; half the resident CTAs per role
-      Plan3d pp = plan3d(G, kModeFwd, c->num_sms, std::max(1, c->occ_pair[G.R] / 2));
-      const long long per_role = static_cast<long long>(c->occ_pair[G.R]) * c->num_sms / 2;
-      pp.grid = dim3(unsigned(2 * std::min<long long>(pp.nitems, per_role)));
-      if (per_role >= 1) {
-        P->pair = true;
-        P->plan_pair = pp;
-        TRY(ar.alloc(&P->progress, size_t(pp.nitems)));
-      }
-    }
-    TbShape sh;
-    if (stencil3d_tb_shape(G.R, &sh) && c->occ_tb[G.R] > 0) {
-      P->tb = true;
-      P->plan_tb = plan_items(G, sh.core_w, sh.core_h, 2 * G.R, c->num_sms, c->occ_tb[G.R]);
-      const Plan3d &pt = P->plan_tb;
-      TRY(ar.alloc(&P->tb_bits, size_t(pt.tiles_x) * pt.tiles_y * G.nzw));
-      TbFlagArgs f;
-      memset(&f, 0, sizeof f);
-      f.tbits = P->tbits;
-      f.nzw = G.nzw;
-      f.flag_tiles_x = G.tiles_x;
-      f.flag_tiles_y = G.tiles_y;
-      f.flag_w = kFlagTX;
-      f.flag_h = kTileFlagTY;
-      f.nx = G.nx;
-      f.ny = G.ny;
-      f.tiles_x = pt.tiles_x;
-      f.tiles_y = pt.tiles_y;
-      f.core_w = sh.core_w;
-      f.core_h = sh.core_h;
-      f.rim_x = sh.rim_x;
-      f.rim_y = G.R;
-      f.region_w = sh.region_w;
-      f.region_h = sh.region_h;
-      f.out = P->tb_bits;
-      CU(launch_tb_flags(c->stream, f));
-      c->launches++;
-    }
   }
   return WP_OK;
 }
@@ -788,8 +758,10 @@ static int prop_step(Prop &P, const Field3 &u, const Field3 &um, float *out, int
     a.nzc = pl.nzc;
     a.nitems = pl.nitems;
     a.err = P.c->d_scalars;
-    const CUtensorMap maps[6] = {u.halo[mode], um.tile[mode], P.b.tile[mode], P.s.tile[mode],
-                                 uj ? uj->tile[mode] : P.b.tile[mode], grad ? grad->tile[mode] : P.b.tile[mode]};
+    a.wait_ns = P.c->wait_ns;
+    const CUtensorMap maps[7] = {u.halo[mode], um.tile[mode], P.b.tile[mode], P.s.tile[mode],
+                                 uj ? uj->tile[mode] : P.b.tile[mode], grad ? grad->tile[mode] : P.b.tile[mode],
+                                 u.tile[mode]};
     if (P.c->hashing) {
       hash_bytes(P.c, &mode, sizeof mode);
       hash_bytes(P.c, &a, sizeof a);
@@ -830,123 +802,6 @@ static int prop_step(Prop &P, const Field3 &u, const Field3 &um, float *out, int
   return WP_OK;
 }
 
-// Two forward steps in one launch: (u^{n-1}, u^n) = (um, u) -> (u^{n+1}, u^{n+2}) =
-// (out1, out2), with data row `row` (+ *row_base) of `inj` injected into u^{n+1};
-// the caller injects the next row into out2.
-static int prop_step2(Prop &P, const Field3 &um, const Field3 &u, Field3 &out1, Field3 &out2, const DevPoints &inj,
-                      const float *data, long long row, const long long *row_base) {
-  const Geom &G = P.G;
-  if (!P.tb || !um.tb_mapped || !u.tb_mapped || !P.b.tb_mapped || !P.s.tb_mapped)
-    return fail(WP_ECUDA, "internal error: a field of the two-step stencil has no TMA descriptor");
-  if (inj.ntarget > kTbMaxTargets) return fail(WP_ECUDA, "internal error: too many targets for the two-step stencil");
-  P.c->prof_open = P.c->profiling && (P.c->prof_seq++ % uint64_t(P.c->prof_every)) == 0;
-  if (P.c->prof_open) TRY(prof_mark(P.c));
-  const Plan3d &pl = P.plan_tb;
-  Stencil3dTbArgs a;
-  memset(&a, 0, sizeof a);
-  a.g = G.fg();
-  a.c = P.lc;
-  a.out1 = out1.p;
-  a.out2 = out2.p;
-  a.tile_bits = P.tb_bits;
-  a.nzw = G.nzw;
-  a.tiles_x = pl.tiles_x;
-  a.tiles_y = pl.tiles_y;
-  a.zchunk = pl.zchunk;
-  a.nzc = pl.nzc;
-  a.nitems = pl.nitems;
-  a.err = P.c->d_scalars;
-  a.ntarget = data ? inj.ntarget : 0;
-  a.target = inj.target;
-  a.rowptr = inj.rowptr;
-  a.pid = inj.pid;
-  a.w = inj.cw;
-  a.data = data;
-  a.npts = inj.npts;
-  a.row_base = row_base;
-  a.row = row;
-  a.b = P.b.p;
-  const CUtensorMap maps[6] = {u.tb[0], um.tb[1], P.b.tb[1], P.s.tb[1], P.b.tb[2], P.s.tb[2]};
-  if (P.c->hashing) {
-    hash_bytes(P.c, &a, sizeof a);
-    hash_bytes(P.c, maps, sizeof maps);
-    hash_bytes(P.c, &pl.grid, sizeof pl.grid);
-    return P.c->prof_open ? prof_mark(P.c) : WP_OK;
-  }
-  cudaError_t e = launch_stencil3d_tb(G.R, pl.grid, P.c->stream, maps, a);
-  if (e != cudaSuccess) return fail(WP_ECUDA, "two-step stencil launch failed: %s", cudaGetErrorString(e));
-  P.c->launches++;
-  if (P.c->prof_open) TRY(prof_mark(P.c));
-  if (!P.c->capturing && P.c->prof_used >= 4096) {
-    TRY(ctx_wait(P.c));
-    TRY(prof_collect(P.c));
-  }
-  return WP_OK;
-}
-
-// Two forward steps by the two-role kernel: (u^{n-1}, u^n) = (um, u) -> (out1, out2)
-// with data row `row` (+ *row_base) injected into u^{n+1}; the caller injects the
-// next row into out2.
-static int prop_pair(Prop &P, const Field3 &um, const Field3 &u, Field3 &out1, Field3 &out2, const DevPoints &inj,
-                     const float *data, long long row, const long long *row_base) {
-  const Geom &G = P.G;
-  if (!P.pair || !um.mapped || !u.mapped || !out1.mapped || !P.b.mapped || !P.s.mapped)
-    return fail(WP_ECUDA, "internal error: the pair stencil cannot run on this grid");
-  if (inj.ntarget > kPairMaxTargets) return fail(WP_ECUDA, "internal error: too many targets for the pair stencil");
-  P.c->prof_open = P.c->profiling && (P.c->prof_seq++ % uint64_t(P.c->prof_every)) == 0;
-  const Plan3d &pl = P.plan_pair;
-  Stencil3dArgs a;
-  memset(&a, 0, sizeof a);
-  a.g = G.fg();
-  a.c = P.lc;
-  a.u = u.p;
-  a.out = out1.p;
-  a.grad = out2.p;
-  a.tbits = P.tbits;
-  a.nzw = G.nzw;
-  a.tiles_x = pl.tiles_x;
-  a.tiles_y = pl.tiles_y;
-  a.flag_tiles_x = G.tiles_x;
-  a.flag_tiles_y = G.tiles_y;
-  a.zchunk = pl.zchunk;
-  a.nzc = pl.nzc;
-  a.nitems = pl.nitems;
-  a.err = P.c->d_scalars;
-  a.bx1 = G.nx;
-  a.by1 = G.ny;
-  a.bz1 = G.nz;
-  a.progress = P.progress;
-  a.ntarget = data ? inj.ntarget : 0;
-  a.target = inj.target;
-  a.rowptr = inj.rowptr;
-  a.pid = inj.pid;
-  a.w = inj.cw;
-  a.data = data;
-  a.npts = inj.npts;
-  a.row_base = row_base;
-  a.row = row;
-  a.b = P.b.p;
-  const CUtensorMap maps[6] = {u.halo[0], um.tile[0], P.b.tile[0], P.s.tile[0], out1.halo[0], u.tile[0]};
-  if (P.c->hashing) {
-    hash_bytes(P.c, &a, sizeof a);
-    hash_bytes(P.c, maps, sizeof maps);
-    hash_bytes(P.c, &pl.grid, sizeof pl.grid);
-    if (P.c->prof_open) TRY(prof_mark(P.c));
-    return P.c->prof_open ? prof_mark(P.c) : WP_OK;
-  }
-  CU(cudaMemsetAsync(P.progress, 0, size_t(pl.nitems) * sizeof(unsigned), P.c->stream));
-  if (P.c->prof_open) TRY(prof_mark(P.c));
-  cudaError_t e = launch_stencil3d_pair(G.R, pl.grid, P.c->stream, maps, a);
-  if (e != cudaSuccess) return fail(WP_ECUDA, "pair stencil launch failed: %s", cudaGetErrorString(e));
-  P.c->launches++;
-  if (P.c->prof_open) TRY(prof_mark(P.c));
-  if (!P.c->capturing && P.c->prof_used >= 4096) {
-    TRY(ctx_wait(P.c));
-    TRY(prof_collect(P.c));
-  }
-  return WP_OK;
-}
-
 static int prop_inject(Prop &P, const DevPoints &dp, const float *data, long long row, float *u, float *grad,
                        const float *uj, const long long *row_base = nullptr) {
   if (dp.ntarget == 0) return WP_OK;
@@ -966,6 +821,8 @@ static int prop_inject(Prop &P, const DevPoints &dp, const float *data, long lon
   a.grad = grad;
   a.uj = uj;
   a.neg_inv_dt2 = P.neg_inv_dt2;
+  a.nfield = P.G.nfield;
+  a.err = P.c->d_scalars;
   if (P.c->hashing) {
     hash_bytes(P.c, &a, sizeof a);
     return WP_OK;
@@ -988,6 +845,8 @@ static int prop_sample(Prop &P, const DevPoints &dp, const float *u, float *out,
   a.out = out;
   a.row_base = row_base;
   a.row = row;
+  a.nfield = P.G.nfield;
+  a.err = P.c->d_scalars;
   if (P.c->hashing) {
     hash_bytes(P.c, &a, sizeof a);
     return WP_OK;
@@ -1143,74 +1002,6 @@ static int run_loop(Prop &P, Field3 u[2], int nt, const DevPoints &inj, const fl
   return WP_OK;
 }
 
-// Whether the time loop can take two steps per launch (3D, the two-step kernel
-// covers the order, few enough injection targets, switched on).
-static bool two_step_ok(const Prop &P, const DevPoints &inj, int nt) {
-  if (P.G.ndim != 3 || nt < 2) return false;
-  if (P.c->temporal_blocking == 1) return P.tb && inj.ntarget <= kTbMaxTargets;
-  if (P.c->temporal_blocking == 2) return P.pair && inj.ntarget <= kPairMaxTargets;
-  return false;
-}
-
-// The same time loop two steps per stencil launch, over four fields: the pair
-// (u[0], u[1]) = (u^{k-1}, u^k) steps into (u[2], u[3]) and back.  Each pair
-// launches the two-step kernel (row k injected inside), injects row k + 1 into
-// u^{k+2} and samples both levels; blocks of B steps (B a multiple of 4, so the
-// buffer parity repeats) are graph replays.  An odd last step runs single.
-static int run_loop2(Prop &P, Field3 u[4], int nt, const DevPoints &inj, const float *data, const DevPoints &smp,
-                     float *out, int dir) {
-  wp_ctx *c = P.c;
-  auto pair = [&](int j, long long ra, long long rb_, const long long *base) -> int {
-    Field3 &um = u[(j & 1) ? 2 : 0], &uc = u[(j & 1) ? 3 : 1];
-    Field3 &o1 = u[(j & 1) ? 0 : 2], &o2 = u[(j & 1) ? 1 : 3];
-    if (c->temporal_blocking == 2)
-      TRY(prop_pair(P, um, uc, o1, o2, inj, data, ra, base));
-    else
-      TRY(prop_step2(P, um, uc, o1, o2, inj, data, ra, base));
-    TRY(prop_inject(P, inj, data, rb_, o2.p, nullptr, nullptr, base));
-    if (out) {
-      TRY(prop_sample(P, smp, o1.p, out, ra, base));
-      TRY(prop_sample(P, smp, o2.p, out, rb_, base));
-    }
-    return WP_OK;
-  };
-  int k0 = 0;
-  int B = 0;
-  if (c->use_graphs && nt >= 16) {
-    int best_rem = nt;
-    for (int b = 64; b >= 8; b -= 4)
-      if (nt % b < best_rem) {
-        B = b;
-        best_rem = nt % b;
-      }
-  }
-  if (B > 0) {
-    long long *rb = c->d_rows;
-    CU(launch_set_row(c->stream, rb, dir > 0 ? 0 : nt - 1));
-    c->launches++;
-    auto block = [&]() -> int {
-      for (int j = 0; j < B / 2; ++j) TRY(pair(j, dir * 2 * j, dir * (2 * j + 1), rb));
-      return prop_add_row(c, rb, static_cast<long long>(dir) * B);
-    };
-    TRY(graph_replay(c, block, nt / B));
-    k0 = (nt / B) * B;
-  }
-  int k = k0;
-  for (; k + 2 <= nt; k += 2) {
-    const long long ra = dir > 0 ? k : nt - 1 - k, rb_ = dir > 0 ? k + 1 : nt - 2 - k;
-    TRY(pair(k / 2, ra, rb_, nullptr));
-  }
-  if (k < nt) {  // one step left: the pair parity says where (u^{k-1}, u^k) are
-    const long long row = dir > 0 ? k : nt - 1 - k;
-    const int j = k / 2;
-    Field3 &prv = u[(j & 1) ? 2 : 0], &cur = u[(j & 1) ? 3 : 1];
-    TRY(prop_step(P, cur, prv, prv.p, kModeFwd, nullptr, nullptr));
-    TRY(prop_inject(P, inj, data, row, prv.p, nullptr, nullptr));
-    if (out) TRY(prop_sample(P, smp, prv.p, out, row));
-  }
-  return WP_OK;
-}
-
 // ---------------------------------------------------------------------------
 // common call prologue
 // ---------------------------------------------------------------------------
@@ -1238,6 +1029,37 @@ static int leave(wp_ctx *c, void *user_stream, int rc) {
   return rc;
 }
 
+// Device-array arguments must be device (or managed) memory of `device`: a host
+// pointer, or memory of another GPU, would be dereferenced by every kernel of
+// the call.  NULL passes (the callers check which arrays are required).
+struct DevArg {
+  const void *p;
+  const char *what;
+};
+static int check_dev_args(int device, std::initializer_list<DevArg> args) {
+  for (const DevArg &a : args) {
+    if (!a.p) continue;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, a.p);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(WP_EINVAL, "%s is not a CUDA device address (%s)", a.what, cudaGetErrorString(e));
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+      return fail(WP_EINVAL, "%s must be device memory (a host pointer was passed to a device-array call)", a.what);
+    if (at.type == cudaMemoryTypeDevice && at.device != device)
+      return fail(WP_EINVAL, "%s lives on device %d, the call runs on device %d", a.what, at.device, device);
+  }
+  return WP_OK;
+}
+
+// In an entry point after enter(): reject bad device-array arguments through leave().
+#define DEV_ARGS(ctx, stream, ...)                                \
+  do {                                                            \
+    int rc_ = check_dev_args((ctx)->device, __VA_ARGS__);         \
+    if (rc_ != WP_OK) return leave((ctx), (stream), rc_);         \
+  } while (0)
+
 static bool all_finite(const float *x, size_t n) {
   for (size_t i = 0; i < n; ++i)
     if (!std::isfinite(x[i])) return false;
@@ -1251,6 +1073,7 @@ static bool all_finite(const float *x, size_t n) {
 static int do_propagate(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *inj_data,
                         int ninj, const double *inj_xyz, int nsmp, const double *smp_xyz, float *smp_out, int dir,
                         bool host_io) {
+  NvtxRange range(dir > 0 ? "wp.forward" : "wp.adjoint");
   Geom G;
   TRY(make_geom(grid, &G));
   if (ninj < 0 || nsmp < 0) return fail(WP_EINVAL, "point counts must be >= 0");
@@ -1301,16 +1124,8 @@ static int do_propagate(wp_ctx *c, const wp_grid *grid, const float *m, const fl
     TRY(ctx_wait(c));
     if (c->h_scalars[1]) return fail(WP_ENONFINITE, "injected data holds NaN or Inf");
   }
-  if (two_step_ok(P, din, G.nt)) {
-    Field3 u4[4];
-    u4[0] = u[0];
-    u4[1] = u[1];
-    TRY(alloc_field(ar, G, &u4[2], false, c->stream));
-    TRY(alloc_field(ar, G, &u4[3], false, c->stream));
-    TRY(run_loop2(P, u4, G.nt, din, data_d, dsm, n_out ? out_d : nullptr, dir));
-  } else {
-    TRY(run_loop(P, u, G.nt, din, data_d, dsm, n_out ? out_d : nullptr, dir));
-  }
+  TRY(run_loop(P, u, G.nt, din, data_d, dsm, n_out ? out_d : nullptr, dir));
+  for (int i = 0; i < 2; ++i) CU(launch_check_padding(c->stream, u[i].p, G.fg(), c->d_scalars));
   if (host_io && n_out) CU(cudaMemcpyAsync(smp_out, out_d, n_out * 4, cudaMemcpyDeviceToHost, c->stream));
   return ctx_wait(c, dir > 0 ? "forward time loop" : "adjoint time loop");
 }
@@ -1341,6 +1156,7 @@ static void state_release(wp_state *st) {
 static int forward_save(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *wavelet,
                         int nsrc, const double *src_xyz, int nrec, const double *rec_xyz, int snap_interval,
                         float *rec_out, bool host_in, bool host_rec, wp_state **out) {
+  NvtxRange range("wp.forward_save");
   const bool host_io = host_in;
   *out = nullptr;
   wp_state *st = new wp_state();
@@ -1458,6 +1274,7 @@ static int forward_save(wp_ctx *c, const wp_grid *grid, const float *m, const fl
 
 // host_res: the residual is a host array; host_grad: grad_out is a host array.
 static int backward(wp_state *st, const float *residual, float *grad_out, bool host_res, bool host_grad) {
+  NvtxRange range("wp.backward");
   const bool host_io = host_res;
   wp_ctx *c = st->c;
   const Geom &G = st->G;
@@ -1515,10 +1332,14 @@ static int backward(wp_state *st, const float *residual, float *grad_out, bool h
     const float *snap = st->snaps + size_t(s) * 2 * G.nfield;
     CU(cudaMemcpyAsync(ring[0].p, snap, G.field_bytes(), cudaMemcpyDeviceToDevice, c->stream));
     CU(cudaMemcpyAsync(ring[1].p, snap + G.nfield, G.field_bytes(), cudaMemcpyDeviceToDevice, c->stream));
-    for (int i = 0; i < len; ++i) {  // recompute u^{s0+1} .. u^{s0+len} into ring[2..]
-      TRY(prop_step(P, ring[i + 1], ring[i], ring[i + 2].p, kModeFwd, nullptr, nullptr));
-      TRY(prop_inject(P, st->dsrc, st->wavelet, s0 + i, ring[i + 2].p, nullptr, nullptr));
+    {
+      NvtxRange rr("wp.recompute");
+      for (int i = 0; i < len; ++i) {  // recompute u^{s0+1} .. u^{s0+len} into ring[2..]
+        TRY(prop_step(P, ring[i + 1], ring[i], ring[i + 2].p, kModeFwd, nullptr, nullptr));
+        TRY(prop_inject(P, st->dsrc, st->wavelet, s0 + i, ring[i + 2].p, nullptr, nullptr));
+      }
     }
+    NvtxRange ra("wp.adjoint_gradient");
     for (int j = s0 + len; j >= s0 + 1; --j, ++kadj) {
       Field3 &w1 = w[kadj & 1], &w2 = w[(kadj + 1) & 1];
       const Field3 &uj = ring[j - s0 + 1];
@@ -1653,10 +1474,6 @@ int wp_create(wp_ctx **out, int device, size_t budget) {
       CU(prepare_stencil3d_fwd(R, &c->smem3d[0][R], &c->occ3d[0][R], &c->ty3d[0][R]));
       CU(prepare_stencil3d_adj(R, &c->smem3d[1][R], &c->occ3d[1][R], &c->ty3d[1][R]));
     }
-    for (int R = 1; R <= 4; ++R) CU(prepare_stencil3d_tb(R, &c->smem_tb[R], &c->occ_tb[R]));
-    for (int R = 1; R <= 4; ++R) CU(prepare_stencil3d_pair(R, &c->smem_pair[R], &c->occ_pair[R]));
-    const char *tbe = getenv("WP_TEMPORAL_BLOCKING");
-    c->temporal_blocking = tbe ? std::max(0, std::min(2, atoi(tbe))) : 0;
     return WP_OK;
   }();
   if (rc != WP_OK) {
@@ -1802,6 +1619,7 @@ int wp_convection_2d(wp_ctx *c, int nx, int ny, double dx, double dy, double dt,
 int wp_convection_2d_dev(wp_ctx *c, int nx, int ny, double dx, double dy, double dt, double cs, int nt,
                          const float *u0, float *u_out, void *stream) {
   TRY(enter(c, stream));
+  DEV_ARGS(c, stream, {{u0, "u0"}, {u_out, "u_out"}});
   return leave(c, stream, convection_impl(c, nx, ny, dx, dy, dt, cs, nt, u0, u_out, false));
 }
 
@@ -1814,6 +1632,7 @@ int wp_burgers_2d(wp_ctx *c, int nx, int ny, double dx, double dy, double dt, do
 int wp_burgers_2d_dev(wp_ctx *c, int nx, int ny, double dx, double dy, double dt, double nu, int nt, const float *u0,
                       const float *v0, float *u_out, float *v_out, void *stream) {
   TRY(enter(c, stream));
+  DEV_ARGS(c, stream, {{u0, "u0"}, {v0, "v0"}, {u_out, "u_out"}, {v_out, "v_out"}});
   return leave(c, stream, burgers_impl(c, nx, ny, dx, dy, dt, nu, nt, u0, v0, u_out, v_out, false));
 }
 
@@ -1826,13 +1645,14 @@ int wp_poisson_2d(wp_ctx *c, int nx, int ny, double dx, double dy, int nit, cons
 int wp_poisson_2d_dev(wp_ctx *c, int nx, int ny, double dx, double dy, int nit, const float *p0, const float *b,
                       float *p_out, void *stream) {
   TRY(enter(c, stream));
+  DEV_ARGS(c, stream, {{p0, "p0"}, {b, "b"}, {p_out, "p_out"}});
   return leave(c, stream, poisson_impl(c, nx, ny, dx, dy, nit, p0, b, p_out, false));
 }
 
-int wp_set_temporal_blocking(wp_ctx *c, int mode) {
+int wp_set_wait_limit(wp_ctx *c, double seconds) {
   if (!c) return fail(WP_EINVAL, "context is NULL");
-  if (mode < 0 || mode > 2) return fail(WP_EINVAL, "temporal blocking mode must be 0, 1 or 2");
-  c->temporal_blocking = mode;
+  if (!(seconds >= 0.0) || seconds > 60.0) return fail(WP_EINVAL, "wait limit must be in [0, 60] s");
+  c->wait_ns = static_cast<uint64_t>(seconds * 1e9);
   return WP_OK;
 }
 
@@ -1905,6 +1725,7 @@ int wp_estimate_bytes(const wp_grid *grid, int nsrc, int nrec, int mode, int sna
 int wp_forward_dev(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *wavelet, int nsrc,
                    const double *src, int nrec, const double *rec, float *rec_out, void *stream) {
   TRY(enter(c, stream));
+  DEV_ARGS(c, stream, {{m, "m"}, {eta, "eta"}, {wavelet, "wavelet"}, {rec_out, "rec_out"}});
   return leave(c, stream, do_propagate(c, grid, m, eta, wavelet, nsrc, src, nrec, rec, rec_out, +1, false));
 }
 
@@ -1917,6 +1738,7 @@ int wp_forward(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta,
 int wp_adjoint_dev(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, const float *rec_data, int nrec,
                    const double *rec, int nsrc, const double *src, float *src_out, void *stream) {
   TRY(enter(c, stream));
+  DEV_ARGS(c, stream, {{m, "m"}, {eta, "eta"}, {rec_data, "rec_data"}, {src_out, "src_out"}});
   return leave(c, stream, do_propagate(c, grid, m, eta, rec_data, nrec, rec, nsrc, src, src_out, -1, false));
 }
 
@@ -1947,6 +1769,8 @@ int wp_gradient_dev(wp_ctx *c, const wp_grid *grid, const float *m, const float 
                     const double *src, const float *residual, int nrec, const double *rec, int S, float *grad_out,
                     void *stream) {
   TRY(enter(c, stream));
+  DEV_ARGS(c, stream, {{m, "m"}, {eta, "eta"}, {wavelet, "wavelet"},
+                                                  {residual, "residual"}, {grad_out, "grad_out"}});
   return leave(c, stream,
                gradient_impl(c, grid, m, eta, wavelet, nsrc, src, residual, nrec, rec, S, grad_out, false));
 }
@@ -2076,6 +1900,7 @@ static int grad_copy_out(wp_ctx *c, const Geom &G, const Field3 &g, float *grad_
 static int gradient_ckpt_impl(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta,
                               const float *wavelet, int nsrc, const double *src, const float *residual, int nrec,
                               const double *rec, int nslots, float *grad_out, bool host_io) {
+  NvtxRange range("wp.gradient_checkpointed");
   if (nslots < 0 || nslots > 4096) return fail(WP_EINVAL, "checkpoints must be in [0, 4096]");
   GradSetup S(c);
   TRY(grad_setup(c, grid, m, eta, wavelet, nsrc, src, residual, nrec, rec, grad_out, host_io, S));
@@ -2189,6 +2014,7 @@ static RingBoxes ring_boxes(const Geom &G, const Box &Z) {
 static int gradient_recon_impl(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta,
                                const float *wavelet, int nsrc, const double *src, const float *residual, int nrec,
                                const double *rec, float *grad_out, bool host_io) {
+  NvtxRange range("wp.gradient_reconstruct");
   GradSetup S(c);
   TRY(grad_setup(c, grid, m, eta, wavelet, nsrc, src, residual, nrec, rec, grad_out, host_io, S));
   const Geom &G = S.G;
@@ -2258,6 +2084,7 @@ int wp_forward_save(wp_ctx *c, const wp_grid *grid, const float *m, const float 
   if (!state) return fail(WP_EINVAL, "state is NULL");
   *state = nullptr;
   TRY(enter(c, stream));
+  DEV_ARGS(c, stream, {{m, "m"}, {eta, "eta"}, {wavelet, "wavelet"}, {rec_out, "rec_out"}});
   return leave(c, stream,
                forward_save(c, grid, m, eta, wavelet, nsrc, src, nrec, rec, S, rec_out, false, false, state));
 }
@@ -2265,6 +2092,7 @@ int wp_forward_save(wp_ctx *c, const wp_grid *grid, const float *m, const float 
 int wp_backward(wp_state *st, const float *residual, float *grad_out, void *stream) {
   if (!st) return fail(WP_EINVAL, "state is NULL");
   TRY(enter(st->c, stream));
+  DEV_ARGS(st->c, stream, {{residual, "residual"}, {grad_out, "grad_out"}});
   return leave(st->c, stream, backward(st, residual, grad_out, false, false));
 }
 
@@ -2280,6 +2108,8 @@ int wp_fwi_gradient_dev(wp_ctx *c, const wp_grid *grid, const float *m, const fl
                         int nsrc, const double *src, const float *d_obs, int nrec, const double *rec, int S,
                         float *grad_out, double *misfit, void *stream) {
   TRY(enter(c, stream));
+  DEV_ARGS(c, stream, {{m, "m"}, {eta, "eta"}, {wavelet, "wavelet"}, {d_obs, "d_obs"},
+                                                  {grad_out, "grad_out"}});
   return leave(c, stream,
                fwi_gradient_impl(c, grid, m, eta, wavelet, nsrc, src, d_obs, nrec, rec, S, grad_out, misfit, false));
 }
@@ -2296,6 +2126,8 @@ int wp_gradient_checkpointed_dev(wp_ctx *c, const wp_grid *grid, const float *m,
                                  const float *wavelet, int nsrc, const double *src, const float *residual, int nrec,
                                  const double *rec, int checkpoints, float *grad_out, void *stream) {
   TRY(enter(c, stream));
+  DEV_ARGS(c, stream, {{m, "m"}, {eta, "eta"}, {wavelet, "wavelet"},
+                                                  {residual, "residual"}, {grad_out, "grad_out"}});
   return leave(c, stream, gradient_ckpt_impl(c, grid, m, eta, wavelet, nsrc, src, residual, nrec, rec, checkpoints,
                                              grad_out, false));
 }
@@ -2312,6 +2144,8 @@ int wp_gradient_reconstruct_dev(wp_ctx *c, const wp_grid *grid, const float *m, 
                                 const float *wavelet, int nsrc, const double *src, const float *residual, int nrec,
                                 const double *rec, float *grad_out, void *stream) {
   TRY(enter(c, stream));
+  DEV_ARGS(c, stream, {{m, "m"}, {eta, "eta"}, {wavelet, "wavelet"},
+                                                  {residual, "residual"}, {grad_out, "grad_out"}});
   return leave(c, stream,
                gradient_recon_impl(c, grid, m, eta, wavelet, nsrc, src, residual, nrec, rec, grad_out, false));
 }
@@ -2342,10 +2176,39 @@ int wp_checkpoint_schedule(int nt, int checkpoints, int *ops, int max_ops, int *
 int wp_axpy_dev(wp_ctx *c, long long n, float alpha, const float *x, float *y, void *stream) {
   if (n < 0 || (n > 0 && (!x || !y))) return fail(WP_EINVAL, "bad axpy arguments");
   TRY(enter(c, stream));
+  DEV_ARGS(c, stream, {{x, "x"}, {y, "y"}});
   int rc = [&]() -> int {
     CU(launch_axpy(c->stream, n, alpha, x, y));
     c->launches++;
     return ctx_wait(c, "axpy");
+  }();
+  return leave(c, stream, rc);
+}
+
+int wp_misfit_dev(wp_ctx *c, long long n, const float *d, const float *d_obs, float *r_out, double *misfit,
+                  void *stream) {
+  if (n < 0 || (n > 0 && (!d || !d_obs || !r_out)) || !misfit) return fail(WP_EINVAL, "bad misfit arguments");
+  TRY(enter(c, stream));
+  DEV_ARGS(c, stream, {{d, "d"}, {d_obs, "d_obs"}, {r_out, "r_out"}});
+  int rc = [&]() -> int {
+    double J = 0.0;
+    if (n) {
+      Arena tmp(c);
+      double *partial = nullptr;
+      const int max_blocks = 1024;
+      TRY(tmp.alloc(&partial, size_t(max_blocks)));
+      int used = 0;
+      CU(launch_residual(c->stream, d, d_obs, r_out, n, partial, max_blocks, &used));
+      c->launches++;
+      std::vector<double> h(static_cast<size_t>(used));
+      CU(cudaMemcpyAsync(h.data(), partial, size_t(used) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      TRY(ctx_wait(c, "misfit"));
+      for (double v : h) J += v;
+      J *= 0.5;
+    }
+    *misfit = J;
+    if (!std::isfinite(J)) return fail(WP_ENONFINITE, "d or d_obs holds NaN or Inf");
+    return WP_OK;
   }();
   return leave(c, stream, rc);
 }
@@ -2355,6 +2218,7 @@ int wp_update_model_dev(wp_ctx *c, long long n, float step, const float *grad, f
   if (n < 0 || (n > 0 && (!grad || !m)) || !(m_min > 0.f) || !(m_max >= m_min))
     return fail(WP_EINVAL, "bad model-update arguments");
   TRY(enter(c, stream));
+  DEV_ARGS(c, stream, {{grad, "grad"}, {m, "m"}});
   int rc = [&]() -> int {
     CU(launch_update_model(c->stream, n, step, grad, m, m_min, m_max));
     c->launches++;
@@ -2392,6 +2256,7 @@ void wp_state_free(wp_state *st) {
 int wp_propagate_dev(wp_ctx *c, const wp_grid *grid, const float *m, const float *eta, float *u_prev, float *u,
                      int nsteps, void *stream) {
   TRY(enter(c, stream));
+  DEV_ARGS(c, stream, {{m, "m"}, {eta, "eta"}, {u_prev, "u_prev"}, {u, "u"}});
   int rc = [&]() -> int {
     Geom G;
     TRY(make_geom(grid, &G));
@@ -2483,14 +2348,23 @@ static void csr_of(const PointSet &ps, std::vector<long long> &target, std::vect
   rowptr.push_back(int(ne));
 }
 
-static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta, const float *wavelet, int nsrc,
-                           const double *src, int nrec, const double *rec, float *rec_out, cudaStream_t st) {
+// `touched` is set once the call has queued work on `st`.
+static int forward_noalloc_body(const wp_grid *grid, const float *m, const float *eta, const float *wavelet,
+                                int nsrc, const double *src, int nrec, const double *rec, float *rec_out,
+                                cudaStream_t st, bool *touched) {
+  NvtxRange range("wp.forward_noalloc");
   Geom G;
   TRY(make_geom(grid, &G));
   if (nsrc < 0 || nrec < 0) return fail(WP_EINVAL, "point counts must be >= 0");
   if (!m || !eta) return fail(WP_EINVAL, "m and eta must not be NULL");
   if (nsrc > 0 && G.nt > 0 && !wavelet) return fail(WP_EINVAL, "wavelet is NULL");
   if (nrec > 0 && G.nt > 0 && !rec_out) return fail(WP_EINVAL, "rec_out is NULL");
+  // everything runs on the current device: the arrays and the stream must belong to it
+  int dev = 0, sdev = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaStreamGetDevice(st, &sdev));
+  if (sdev != dev) return fail(WP_EINVAL, "the stream belongs to device %d, the current device is %d", sdev, dev);
+  TRY(check_dev_args(dev, {{m, "m"}, {eta, "eta"}, {wavelet, "wavelet"}, {rec_out, "rec_out"}}));
   PointSet ps, pr;
   TRY(build_points(G, nsrc, src, &ps, "source"));
   TRY(build_points(G, nrec, rec, &pr, "receiver"));
@@ -2535,6 +2409,7 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
   plan(c, &scal, &b, &s, &u0, &u1, &tbits, &tflag, &d_target, &d_rowptr, &d_pid, &d_cw, &d_ridx, &d_rw);
 
   // the array keeps the last call's contents: clear what must start at zero
+  *touched = true;
   CU(cudaMemsetAsync(scal, 0, 16 * sizeof(int), st));
   if (tflag) CU(cudaMemsetAsync(tflag, 0, size_t(G.nz) * G.tiles_y * G.tiles_x, st));
   if (!target.empty()) {
@@ -2593,9 +2468,8 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
     }
     TRY(make_map(&tb, b, G, tx, ty));
     TRY(make_map(&ts, s, G, tx, ty));
-    int smem = 0, occ = 0, ty_k = 0, dev = 0, nsm = 0;
+    int smem = 0, occ = 0, ty_k = 0, nsm = 0;
     CU(prepare_stencil3d_fwd(G.R, &smem, &occ, &ty_k));
-    CU(cudaGetDevice(&dev));
     CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     pl = plan3d(G, kModeFwd, nsm, occ);
   }
@@ -2623,7 +2497,8 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
       a.bx1 = G.nx;  // the whole grid
       a.by1 = G.ny;
       a.bz1 = G.nz;
-      const CUtensorMap maps[6] = {halo[k & 1], tile[(k + 1) & 1], tb, ts, tb, tb};
+      a.wait_ns = kWaitLimitNs;
+      const CUtensorMap maps[7] = {halo[k & 1], tile[(k + 1) & 1], tb, ts, tb, tb, tile[k & 1]};
       CU(launch_stencil3d_fwd(G.R, pl.grid, st, maps, a));
     } else {
       Stencil2dArgs a;
@@ -2657,6 +2532,8 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
       ia.grad = nullptr;
       ia.uj = nullptr;
       ia.neg_inv_dt2 = neg_inv_dt2;
+      ia.nfield = G.nfield;
+      ia.err = scal;
       CU(launch_inject(st, ia));
     }
     if (nrec > 0) {
@@ -2670,18 +2547,25 @@ static int forward_noalloc(const wp_grid *grid, const float *m, const float *eta
       pa.u = prv;
       pa.out = rec_out;
       pa.row = k;
+      pa.nfield = G.nfield;
+      pa.err = scal;
       CU(launch_interp(st, pa));
     }
   }
   CU(cudaMemcpyAsync(h, scal, sizeof h, cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
-  if (h[0] != 0) return fail(WP_EDEVICE, "a kernel reported device error %d (a wait timed out)", h[0]);
+  if (h[0] != 0) return fail(WP_EDEVICE, "a kernel reported device error %d: %s", h[0], device_error_text(h[0]));
   return WP_OK;
 }
 
 extern "C" int wp_forward_noalloc(const wp_grid *grid, const float *m, const float *eta, const float *wavelet,
                                   int nsrc, const double *src_coords, int nrec, const double *rec_coords,
                                   float *rec_out, void *stream) {
-  return forward_noalloc(grid, m, eta, wavelet, nsrc, src_coords, nrec, rec_coords, rec_out,
-                         static_cast<cudaStream_t>(stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  bool touched = false;
+  const int rc = forward_noalloc_body(grid, m, eta, wavelet, nsrc, src_coords, nrec, rec_coords, rec_out, st, &touched);
+  // after an error, let whatever was queued finish before the caller may reuse the
+  // work space (a failed launch leaves earlier kernels running on it)
+  if (rc != WP_OK && touched) cudaStreamSynchronize(st);
+  return rc;
 }

@@ -215,41 +215,6 @@ cudaError_t launch_check_finite(cudaStream_t st, const float *x, long long n, in
 }
 
 // ---------------------------------------------------------------------------
-// Damping words of the two-step stencil's tiles (one thread per tile and word)
-// ---------------------------------------------------------------------------
-__global__ void tb_flags_kernel(const TbFlagArgs a) {
-  const long long n = static_cast<long long>(a.tiles_x) * a.tiles_y * a.nzw;
-  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-  if (i >= n) return;
-  const int w = static_cast<int>(i % a.nzw);
-  const int tile = static_cast<int>(i / a.nzw);
-  const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-  const int gx0 = tx * a.core_w, gy0 = ty * a.core_h;
-  auto word = [&](int x0, int x1, int y0, int y1) -> unsigned {
-    x0 = max(x0, 0);
-    y0 = max(y0, 0);
-    x1 = min(x1, a.nx);
-    y1 = min(y1, a.ny);
-    unsigned m = 0;
-    if (x0 >= x1 || y0 >= y1) return 0u;
-    for (int fy = y0 / a.flag_h; fy <= (y1 - 1) / a.flag_h && fy < a.flag_tiles_y; ++fy)
-      for (int fx = x0 / a.flag_w; fx <= (x1 - 1) / a.flag_w && fx < a.flag_tiles_x; ++fx)
-        m |= a.tbits[(static_cast<long long>(fy) * a.flag_tiles_x + fx) * a.nzw + w];
-    return m;
-  };
-  const int rx0 = gx0 - a.rim_x, ry0 = gy0 - a.rim_y;
-  a.out[i] = make_uint2(word(rx0, rx0 + a.region_w, ry0, ry0 + a.region_h),
-                        word(gx0, gx0 + a.core_w, gy0, gy0 + a.core_h));
-}
-
-cudaError_t launch_tb_flags(cudaStream_t st, const TbFlagArgs &a) {
-  const long long n = static_cast<long long>(a.tiles_x) * a.tiles_y * a.nzw;
-  if (n <= 0) return cudaSuccess;
-  tb_flags_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(a);
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
 // Boundary-wavefield reconstruction helpers: the box where eta vanishes, the
 // ring of stored boundary values around it, and the mask of the gradient.
 // ---------------------------------------------------------------------------
@@ -380,7 +345,9 @@ __global__ void inject_kernel(const InjectArgs a) {
   float acc = 0.f;
   for (int k = a.rowptr[i]; k < a.rowptr[i + 1]; ++k) acc = fmaf(a.w[k], q[a.pid[k]], acc);
   const long long t = a.target[i];
-  // explicit roundings (no contraction): the two-step stencil repeats this arithmetic
+  if (!WP_IN_BOUNDS(t >= 0 && t < a.nfield, a.err)) return;
+  // explicit roundings (no contraction), so the result does not depend on how the
+  // compiler fuses this expression
   const float inc = __fmul_rn(a.b[t], acc);
   a.u[t] = __fadd_rn(a.u[t], inc);
   if (a.grad) a.grad[t] = fmaf(a.neg_inv_dt2 * a.uj[t], inc, a.grad[t]);
@@ -399,10 +366,41 @@ __global__ void interp_kernel(const InterpArgs a) {
   float acc = 0.f;
   for (int c = 0; c < a.ncorner; ++c) {
     const long long k = static_cast<long long>(i) * a.ncorner + c;
+    if (!WP_IN_BOUNDS(a.idx[k] >= 0 && a.idx[k] < a.nfield, a.err)) return;
     acc = fmaf(a.w[k], a.u[a.idx[k]], acc);
   }
   const long long row = a.row + (a.row_base ? *a.row_base : 0);
   a.out[row * a.npts + i] = acc;
+}
+
+#ifdef WP_DEBUG_BOUNDS
+__global__ void check_padding_kernel(const float *f, FieldGeom g, int *err) {
+  const int pad = g.pitch - g.nx;
+  const long long rows = static_cast<long long>(g.ny) * g.nz;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < rows * pad;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long row = i / pad;
+    const int x = g.nx + static_cast<int>(i - row * pad);
+    if (f[row * g.pitch + x] != 0.f) {
+      atomicCAS(err, 0, static_cast<int>(kErrBounds));
+      return;
+    }
+  }
+}
+#endif
+
+cudaError_t launch_check_padding(cudaStream_t st, const float *f, FieldGeom g, int *err) {
+#ifdef WP_DEBUG_BOUNDS
+  if (g.pitch == g.nx) return cudaSuccess;
+  check_padding_kernel<<<152 * 4, 256, 0, st>>>(f, g, err);
+  return cudaGetLastError();
+#else
+  (void)st;
+  (void)f;
+  (void)g;
+  (void)err;
+  return cudaSuccess;
+#endif
 }
 
 cudaError_t launch_interp(cudaStream_t st, const InterpArgs &a) {

@@ -10,8 +10,8 @@ namespace wp {
 
 struct Stencil3dArgs;
 
-// ---- K1, 3D (stencil3d_fwd.cu / stencil3d_adj.cu) ----
-// maps: u^n (halo'd plane box of the mode), u^{n-1}, b, s, u^j, g (tile boxes of the mode)
+// ---- K1, 3D (stencil3d_fwd.cu / stencil3d_adj.cu; half-orders above 4: stencil3d_hi.cu) ----
+// maps: u^n (halo'd plane box of the mode), u^{n-1}, b, s, u^j, g, u^n (tile boxes of the mode)
 cudaError_t launch_stencil3d_fwd(int R, dim3 grid, cudaStream_t st, const CUtensorMap *maps,
                                  const Stencil3dArgs &a);
 cudaError_t launch_stencil3d_adj(int R, dim3 grid, cudaStream_t st, const CUtensorMap *maps,
@@ -30,39 +30,12 @@ inline int stencil3d_tile_x(int R, int mode) {
 inline int stencil3d_tile_y(int R, int mode) {
   return mode == 1 ? stencil3d_tile_y_adj(R) : stencil3d_tile_y_fwd(R);
 }
-
-// ---- K1, 3D, two steps by two CTA roles in one cooperative launch (stencil3d_pair.cu) ----
-// maps: u^n halo, u^{n-1} tile, b, s, u^{n+1} halo, u^n tile (the mode-0 boxes); R <= 4
-cudaError_t launch_stencil3d_pair(int R, dim3 grid, cudaStream_t st, const CUtensorMap *maps,
-                                  const Stencil3dArgs &a);
-cudaError_t prepare_stencil3d_pair(int R, int *smem_bytes, int *blocks_per_sm);
-
-// ---- K1, 3D, two steps per launch (stencil3d_tb.cu) ----
-struct Stencil3dTbArgs;
-// Box sizes of the two-step kernel for half-order R (false if R is not covered).
-struct TbShape {
-  int region_w, region_h;  // step-1 region (u^{n-1}, b, s tiles)
-  int core_w, core_h;      // step-2 core (b, s tiles; output)
-  int rim_x;               // x offset of the core in the region (y offset: R)
-  int plane_w, plane_h;    // halo'd u^n plane box
-};
-bool stencil3d_tb_shape(int R, TbShape *s);
-// maps: u^n (plane box), u^{n-1}, b, s (region boxes), b, s (core boxes)
-cudaError_t launch_stencil3d_tb(int R, dim3 grid, cudaStream_t st, const CUtensorMap *maps,
-                                const Stencil3dTbArgs &a);
-cudaError_t prepare_stencil3d_tb(int R, int *smem_bytes, int *blocks_per_sm);
-
-// Damping words of the two-step kernel's tiles: out[tile][w] = (region word, core
-// word), the OR of the flag-tile bitmasks (bit z of word w: plane 32 w + z damped)
-// over the flag tiles that meet the tile's region / core box.
-struct TbFlagArgs {
-  const unsigned *tbits;
-  int nzw, flag_tiles_x, flag_tiles_y, flag_w, flag_h;
-  int nx, ny;
-  int tiles_x, tiles_y, core_w, core_h, rim_x, rim_y, region_w, region_h;
-  uint2 *out;
-};
-cudaError_t launch_tb_flags(cudaStream_t st, const TbFlagArgs &a);
+// the kernel of half-orders 5..8 (mode 0 forward, 1 adjoint+gradient)
+cudaError_t launch_stencil3d_hi(int R, int mode, dim3 grid, cudaStream_t st, const CUtensorMap *maps,
+                                const Stencil3dArgs &a);
+cudaError_t prepare_stencil3d_hi(int R, int mode, int *smem_bytes, int *blocks_per_sm, int *tile_y);
+int stencil3d_hi_tile_x(int R, int mode);
+int stencil3d_hi_tile_y(int R, int mode);
 
 // ---- K1, 2D (kernels.cu) ----
 struct Stencil2dArgs {
@@ -113,6 +86,8 @@ struct InjectArgs {
   float *grad;               // optional: gradient correction at the targets
   const float *uj;
   float neg_inv_dt2;
+  long long nfield;          // elements of a pitched field (debug bounds checks)
+  int *err;                  // error word (debug bounds checks)
 };
 cudaError_t launch_inject(cudaStream_t st, const InjectArgs &a);
 
@@ -126,8 +101,14 @@ struct InterpArgs {
   float *out;                // [nt][npts]
   const long long *row_base; // optional device row base (graph replays); row is added to it
   long long row;
+  long long nfield;          // elements of a pitched field (debug bounds checks)
+  int *err;                  // error word (debug bounds checks)
 };
 cudaError_t launch_interp(cudaStream_t st, const InterpArgs &a);
+
+// Debug builds: record kErrBounds if any pitch padding element (x in [nx, pitch))
+// of a pitched field is nonzero (nothing may write there).  Release builds: no-op.
+cudaError_t launch_check_padding(cudaStream_t st, const float *f, FieldGeom g, int *err);
 
 // *p = v / *p += d (row bases of graph replays), one thread
 cudaError_t launch_set_row(cudaStream_t st, long long *p, long long v);

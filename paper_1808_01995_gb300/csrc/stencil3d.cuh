@@ -10,8 +10,11 @@
 // Eq. Grad:  g -= dt^-2 u^j [s (w^{j+1} - w^{j+2}) + b Lap w^{j+1}]  (the
 // injected part is added by the injection kernel).
 //
+// This file holds the kernel of space orders up to 8 (half-order R <= 4); the
+// wider stencils have their own layout (stencil3d_hi.cuh).
+//
 // GB300 design.  Persistent CTAs walk (TX x TY tile, z-chunk) work items in a
-// static round-robin order and stream each chunk up z.  A producer warp issues
+// static round-robin order and stream each chunk along z.  A producer warp issues
 // TMA (cp.async.bulk.tensor) loads, P planes ahead of the compute, into two
 // shared rings guarded by full/empty mbarriers:
 //   - the halo'd u^n plane, (TX + 2 RX) x (TY + 2R), ring depth R + 1 + P (TMA's
@@ -23,12 +26,9 @@
 // rows: it loads its column of the plane once for all y neighbours, reads x
 // neighbours from the plane and keeps z neighbours in a register queue.  This
 // keeps both the shared-memory traffic and the instructions issued per point
-// low enough for HBM to be the bound.  Orders above 8 (one CTA per SM, the u ring
-// being R + 1 + P halo'd planes deep) take three rows per lane, three planes in
-// flight and x/y/z partial sums of the Laplacian, for more independent work per
-// warp: those kernels are bound by issue latency, not by HBM.
-// Every wait is bounded (%globaltimer); a timeout sets an abort flag, the
-// producer lets its copies land, and the error word reports it.
+// low enough for HBM to be the bound.
+// Every wait is bounded (%globaltimer, limit a.wait_ns); a timeout sets an abort
+// flag, the producer lets its copies land, and the error word reports it.
 #pragma once
 
 #include <type_traits>
@@ -42,67 +42,44 @@ constexpr int kThreads3d = (kConsumerWarps + 1) * 32;
 constexpr int kFlagTX = 32;                 // x extent of a damping-flag tile
 constexpr int kTileFlagTY = 16;             // y extent of a damping-flag tile
 
-enum StencilMode : int { kModeFwd = 0, kModeAdjGrad = 1, kModePair = 2 };
-
-// Two forward steps by two roles of CTAs in one cooperative launch (kModePair):
-// even CTAs take (u^{n-1}, u^n) -> u^{n+1} exactly as kModeFwd, with the injection
-// of q^n applied at the store, and publish per work item how many planes of u^{n+1}
-// are complete; odd CTAs take (u^n, u^{n+1}) -> u^{n+2} and load a plane of u^{n+1}
-// only once the items that hold it (own column and its four edge neighbours, and
-// the chunk below for the z halo) have published it.  Every CTA is resident and
-// even CTAs never wait, so every awaited item is eventually produced; u^{n+1} is
-// read back from L2 shortly after it is written.
-constexpr int kPairMaxTargets = 64;
-constexpr int kErrWaitPeer = 3;  // a column's progress did not arrive in time
+enum StencilMode : int { kModeFwd = 0, kModeAdjGrad = 1 };
 
 // Tile parameters, chosen by measurement; the -D overrides exist for sweeps.
 #ifndef WP_NX
 #define WP_NX 2          // x points per lane
 #endif
 #ifndef WP_NY_LO
-#define WP_NY_LO 2       // rows per lane, R <= 4
-#endif
-#ifndef WP_NY_HI
-#define WP_NY_HI 3       // rows per lane, R > 4
-#endif
-#ifndef WP_P_HI
-#define WP_P_HI 3        // planes in flight, R > 4
-#endif
-#ifndef WP_MINB_HI
-#define WP_MINB_HI 1     // CTAs per SM the compiler must fit, R > 4
+#define WP_NY_LO 2       // rows per lane
 #endif
 #ifndef WP_MINB_LO
-#define WP_MINB_LO 2     // CTAs per SM the compiler must fit, R <= 4
+#define WP_MINB_LO 2     // CTAs per SM the compiler must fit
 #endif
 #ifndef WP_ZU
 #define WP_ZU 2          // planes per unrolled z step (1..4)
 #endif
 #ifndef WP_P_ADJ
-#define WP_P_ADJ 2       // planes in flight, adjoint+gradient mode, R <= 4 (two CTAs per SM)
+#define WP_P_ADJ 2       // planes in flight, adjoint+gradient mode (two CTAs per SM)
 #endif
 #ifndef WP_ZALT
-#define WP_ZALT 1        // R <= 4: odd z-chunks of a column swept downward (not in kModePair)
-#endif
-#ifndef WP_LAP_SPLIT
-#define WP_LAP_SPLIT 1   // R > 4: accumulate the Laplacian in three partial sums (x, y, z)
+#define WP_ZALT 1        // odd z-chunks of a column swept downward
 #endif
 
 
 template <int R, int MODE>
 struct Cfg3d {
+  static_assert(R >= 1 && R <= 4, "half-orders above 4 use stencil3d_hi_kernel");
   static constexpr int NX = WP_NX;
-  static constexpr int NY = MODE != kModeAdjGrad ? (R <= 4 ? WP_NY_LO : WP_NY_HI) : 2;
+  static constexpr int NY = WP_NY_LO;
   static constexpr int TX = 32 * NX;                                 // tile width
   static constexpr int TY = kConsumerWarps * NY;                     // tile height
   static constexpr int RX = (R + 3) / 4 * 4;                         // x halo rounded to 16 bytes
   static constexpr int RE = (R + 1) / 2 * 2;                         // x window half-width (even)
   static constexpr int PW = TX + 2 * RX;
   static constexpr int PH = TY + 2 * R;
-  static constexpr int P = R > 4 ? WP_P_HI : MODE == kModeAdjGrad ? WP_P_ADJ : 3;  // planes in flight ahead
-  static constexpr int MINB = R <= 4 ? WP_MINB_LO : WP_MINB_HI;      // CTAs per SM to fit
+  static constexpr int P = MODE == kModeAdjGrad ? WP_P_ADJ : 3;      // planes in flight ahead
+  static constexpr int MINB = WP_MINB_LO;                            // CTAs per SM to fit
   static constexpr int ZU = WP_ZU;                                   // planes per unrolled z step
-  static constexpr bool SPLIT = R > 4 && WP_LAP_SPLIT != 0;           // x, y, z partial sums
-  static constexpr bool ZALT = WP_ZALT != 0 && R <= 4 && MODE != kModePair;  // alternate sweep directions
+  static constexpr bool ZALT = WP_ZALT != 0;                         // alternate sweep directions
   static constexpr int NSU = R + 1 + P;                              // u ring depth
   static constexpr int NST = P + 1;                                  // tile ring depth
   static constexpr int NSTREAM = MODE == kModeAdjGrad ? 5 : 3;       // um, b, s [, uj, g]
@@ -110,8 +87,7 @@ struct Cfg3d {
   static constexpr int TSLOT = TX * TY * 4;                          // bytes per tile
   static constexpr int T_OFF = NSU * USLOT;
   static constexpr int BAR_OFF = T_OFF + NST * NSTREAM * TSLOT;
-  static constexpr int TGT_OFF = (BAR_OFF + 2 * (NSU + NST) * 8 + NST * 4 + 16 + 15) / 16 * 16;
-  static constexpr int SMEM = MODE == kModePair ? TGT_OFF + kPairMaxTargets * 16 : BAR_OFF + 2 * (NSU + NST) * 8 + NST * 4 + 16;
+  static constexpr int SMEM = BAR_OFF + 2 * (NSU + NST) * 8 + NST * 4 + 16;
   static_assert(RX >= RE, "x halo must cover the x window");
 };
 
@@ -132,19 +108,7 @@ struct Stencil3dArgs {
   // updated box [bx0, bx1) x [by0, by1) x [bz0, bz1) (the whole grid normally; bx0 a
   // multiple of 4); neighbours outside it are read, only points inside are written
   int bx0, by0, bz0, bx1, by1, bz1;
-  // kModePair: out = u^{n+1}, grad = u^{n+2}; progress[column] = planes of u^{n+1}
-  // complete (zeroed before the launch); injection of data row `row` (+ *row_base)
-  // into u^{n+1} with the arithmetic of the injection kernel
-  unsigned *progress;
-  int ntarget;
-  const long long *target;
-  const int *rowptr, *pid;
-  const float *w;
-  const float *data;
-  int npts;
-  const long long *row_base;
-  long long row;
-  const float *b;
+  unsigned long long wait_ns;   // a wait gives up after this long (0: unless already complete)
 };
 
 // ---- scalar / packed-pair arithmetic -------------------------------------
@@ -188,31 +152,11 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  // kModePair: role 0 computes u^{n+1} from (tm_um, tm_u) into out; role 1 computes
-  // u^{n+2} from (tm_g = u^n tile, tm_uj = u^{n+1} halo) into grad
-  const int role = MODE == kModePair ? static_cast<int>(blockIdx.x & 1u) : 0;
-  const int cta = MODE == kModePair ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
-  const int ncta = MODE == kModePair ? static_cast<int>(gridDim.x >> 1) : static_cast<int>(gridDim.x);
-  const CUtensorMap *map_u = (MODE == kModePair && role) ? &tm_uj : &tm_u;
-  const CUtensorMap *map_um = (MODE == kModePair && role) ? &tm_g : &tm_um;
-  float *const outp = (MODE == kModePair && role) ? a.grad : a.out;
-  // role 0: the injection targets of this CTA's column, (z, y, x, increment)
-  float4 *tgt = reinterpret_cast<float4 *>(smem + C::TGT_OFF);
-  __shared__ int ntgt_col;
-  if (MODE == kModePair && role == 0) {
-    // every injection target (z, y, x, increment); the stores check them
-    if (tid == 0) ntgt_col = a.ntarget;
-    if (tid < a.ntarget) {
-      const long long t = a.target[tid];
-      const int z = static_cast<int>(t / a.g.plane);
-      const long long rem = t - static_cast<long long>(z) * a.g.plane;
-      const int y = static_cast<int>(rem / a.g.pitch), x = static_cast<int>(rem - static_cast<long long>(y) * a.g.pitch);
-      const float *qd = a.data + (a.row + (a.row_base ? *a.row_base : 0)) * a.npts;
-      float acc = 0.f;
-      for (int k = a.rowptr[tid]; k < a.rowptr[tid + 1]; ++k) acc = fmaf(a.w[k], qd[a.pid[k]], acc);
-      tgt[tid] = make_float4(__int_as_float(z), __int_as_float(y), __int_as_float(x), __fmul_rn(a.b[t], acc));
-    }
-  }
+  const int cta = static_cast<int>(blockIdx.x);
+  const int ncta = static_cast<int>(gridDim.x);
+  const CUtensorMap *map_u = &tm_u;
+  const CUtensorMap *map_um = &tm_um;
+  float *const outp = a.out;
   if (tid == 0) {
     for (int i = 0; i < C::NSU; ++i) {
       mbar_init(&full_u[i], 1);
@@ -271,59 +215,14 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
         ok = false;
         return false;
       };
-      // kModePair, role 1: wait until the items holding plane p of u^{n+1} for the
-      // plane box (this column and its four edge neighbours; own column only when
-      // `own`) have published it
-      // (the last value read per column is kept: progress only grows, and the
-      // producing CTAs usually run ahead, so most planes need no poll)
-      int col_tx = 0, col_ty = 0;
-      int seen_key = -1;      // item (column, chunk) the cached values belong to
-      unsigned seen[5] = {0, 0, 0, 0, 0};
-      auto wait_columns = [&](int p, bool own) -> bool {
-        const int c = (p - a.bz0) / a.zchunk;
-        const unsigned need = static_cast<unsigned>(p - (a.bz0 + c * a.zchunk) + 1);
-        const int key = (col_ty * a.tiles_x + col_tx) * a.nzc + c + (own ? 1 << 30 : 0);
-        if (key != seen_key) {
-          seen_key = key;
-          for (int k = 0; k < 5; ++k) seen[k] = 0;
-        }
-        bool polled = false;
-        const uint64_t t0 = global_timer_ns();
-        for (int k = 0; k < (own ? 1 : 5); ++k) {
-          const int cx = col_tx + (k == 1 ? -1 : k == 2 ? 1 : 0), cy = col_ty + (k == 3 ? -1 : k == 4 ? 1 : 0);
-          if (cx < 0 || cx >= a.tiles_x || cy < 0 || cy >= a.tiles_y) continue;
-          if (seen[k] >= need) continue;
-          polled = true;
-          const unsigned *f = a.progress + (static_cast<long long>(cy) * a.tiles_x + cx) * a.nzc + c;
-          while (true) {
-            unsigned v;
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
-            seen[k] = v;
-            if (v >= need) break;
-            if (*abort_flag) return false;
-            if (global_timer_ns() - t0 > kWaitLimitNs) {
-              atomicCAS(a.err, 0, static_cast<int>(kErrWaitPeer));
-              *abort_flag = 1;
-              return false;
-            }
-          }
-        }
-        // the published planes were written by generic stores; the TMA reads them
-        if (polled) asm volatile("fence.proxy.async.global;" ::: "memory");
-        return true;
-      };
       auto issue_u = [&](int x0, int y0, int p) {
         const uint32_t slot = iu % C::NSU;
-        if (iu >= C::NSU && !mbar_wait_bounded(&empty_u[slot], ((iu / C::NSU) - 1) & 1, abort_flag)) {
+        if (iu >= C::NSU && !mbar_wait_bounded(&empty_u[slot], ((iu / C::NSU) - 1) & 1, abort_flag, a.wait_ns)) {
           ok = false;
           return;
         }
         float *dst = uring + slot * (C::USLOT / 4);
         if (!aligned(dst, x0 - C::RX)) return;
-        if (MODE == kModePair && role == 1 && p >= a.bz0 && p < a.bz1 && !wait_columns(p, false)) {
-          ok = false;
-          return;
-        }
         mbar_arrive_expect_tx(&full_u[slot], C::PW * C::PH * 4);
         tma_load_3d(dst, map_u, x0 - C::RX, y0 - R, phys(p), &full_u[slot]);
         ++iu;
@@ -331,7 +230,7 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
       auto issue_t = [&](int x0, int y0, int zs, bool d) {
         const int z = phys(zs);
         const uint32_t slot = itt % C::NST;
-        if (itt >= C::NST && !mbar_wait_bounded(&empty_t[slot], ((itt / C::NST) - 1) & 1, abort_flag)) {
+        if (itt >= C::NST && !mbar_wait_bounded(&empty_t[slot], ((itt / C::NST) - 1) & 1, abort_flag, a.wait_ns)) {
           ok = false;
           return;
         }
@@ -357,16 +256,6 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
         cz1 = z1;
         cdir = dir;
         const int x0 = a.bx0 + tx * TX, y0 = a.by0 + ty * TY;
-        col_tx = tx;
-        col_ty = ty;
-        if (MODE == kModePair && role == 1 && z0 > a.bz0) {  // z halo below: centres read by the consumers
-          bool good = true;
-          for (int p = max(z0 - R, a.bz0); p < z0 && good; ++p) good = wait_columns(p, true);
-          if (!good) {
-            ok = false;
-            break;
-          }
-        }
         // damping bits of the flag tiles covered by this work tile
         const int fx0 = x0 / kFlagTX, fx1 = min((x0 + TX - 1) / kFlagTX + 1, a.flag_tiles_x);
         const int fy0 = y0 / kTileFlagTY, fy1 = min((y0 + TY - 1) / kTileFlagTY + 1, a.flag_tiles_y);
@@ -442,17 +331,10 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
       const int p = phys(z0 - R + j);
 #pragma unroll
       for (int r = 0; r < NY; ++r) {
-        const float *src = (MODE == kModePair && role ? a.out : a.u) + p * a.g.plane + rbase[r];
-        if constexpr (MODE == kModePair) {
-          if (role == 1 && j == 0 && r == 0 && p >= 0)  // the producer has checked the chunk below
-            mbar_wait_bounded(&full_u[ub % C::NSU], (ub / C::NSU) & 1, abort_flag);
-        }
+        const float *src = a.u + p * a.g.plane + rbase[r];
         const bool ok = p >= 0 && p < a.g.nz && yin[r];
         if constexpr (NX == 2) {
-          if (MODE == kModePair && role == 1)  // written by other CTAs of this launch: coherent loads
-            q[r][j] = make_float2(ok && xin0 ? __ldcg(src + gxc0) : 0.f, ok && xin1 ? __ldcg(src + gxc1) : 0.f);
-          else
-            q[r][j] = make_float2(ok && xin0 ? __ldg(src + gxc0) : 0.f, ok && xin1 ? __ldg(src + gxc1) : 0.f);
+          q[r][j] = make_float2(ok && xin0 ? __ldg(src + gxc0) : 0.f, ok && xin1 ? __ldg(src + gxc1) : 0.f);
         } else {
           q[r][j] = ok && xin0 ? __ldg(src + gxc0) : 0.f;
         }
@@ -462,7 +344,7 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
     for (int j = 0; j < R; ++j) {
       const uint32_t pos = ub + j;
       const uint32_t slot = pos % C::NSU;
-      mbar_wait_bounded(&full_u[slot], (pos / C::NSU) & 1, abort_flag);
+      mbar_wait_bounded(&full_u[slot], (pos / C::NSU) & 1, abort_flag, a.wait_ns);
       const float *P = uring + slot * (C::USLOT / 4);
 #pragma unroll
       for (int r = 0; r < NY; ++r) q[r][R + j] = vld<V>(P + (ty0 + r + R) * C::PW + cx0);
@@ -477,7 +359,7 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
         {
           const uint32_t pos = ub + (z + R - z0);
           const uint32_t slot = pos % C::NSU;
-          mbar_wait_bounded(&full_u[slot], (pos / C::NSU) & 1, abort_flag);
+          mbar_wait_bounded(&full_u[slot], (pos / C::NSU) & 1, abort_flag, a.wait_ns);
           const float *P = uring + slot * (C::USLOT / 4);
 #pragma unroll
           for (int r = 0; r < NY; ++r) q[r][2 * R + o] = vld<V>(P + (ty0 + r + R) * C::PW + cx0);
@@ -508,26 +390,11 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
                 if ((j & 1) == 0) return __fadd2_rn(w[(C::RE + j) >> 1], w[(C::RE - j) >> 1]);
                 return make_float2(win(C::RE + j) + win(C::RE - j), win(C::RE + 1 + j) + win(C::RE + 1 - j));
               };
-              if constexpr (C::SPLIT) {
-                // three partial sums (x, y, z) so that no chain of dependent FMAs is longer than R
-                V ly = vmul(vsplat<V>(a.c.cy[1]), ysum(1));
-                V lz = vmul(vsplat<V>(a.c.cz[1]), zsum(1));
 #pragma unroll
-                for (int j = 1; j <= R; ++j) {
-                  l = vfma(vsplat<V>(a.c.cx[j]), xsum(j), l);
-                  if (j > 1) {
-                    ly = vfma(vsplat<V>(a.c.cy[j]), ysum(j), ly);
-                    lz = vfma(vsplat<V>(a.c.cz[j]), zsum(j), lz);
-                  }
-                }
-                l = vadd(l, vadd(ly, lz));
-              } else {
-#pragma unroll
-                for (int j = 1; j <= R; ++j) {
-                  l = vfma(vsplat<V>(a.c.cx[j]), xsum(j), l);
-                  l = vfma(vsplat<V>(a.c.cy[j]), ysum(j), l);
-                  l = vfma(vsplat<V>(a.c.cz[j]), zsum(j), l);
-                }
+              for (int j = 1; j <= R; ++j) {
+                l = vfma(vsplat<V>(a.c.cx[j]), xsum(j), l);
+                l = vfma(vsplat<V>(a.c.cy[j]), ysum(j), l);
+                l = vfma(vsplat<V>(a.c.cz[j]), zsum(j), l);
               }
             } else {
 #pragma unroll
@@ -544,7 +411,7 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
 
         // pointwise tiles of plane z
         const uint32_t tslot = tpos % C::NST;
-        mbar_wait_bounded(&full_t[tslot], (tpos / C::NST) & 1, abort_flag);
+        mbar_wait_bounded(&full_t[tslot], (tpos / C::NST) & 1, abort_flag, a.wait_ns);
         ++tpos;
         const float *T = tring + tslot * (C::NSTREAM * TT);
         const bool d = sflag[tslot] != 0;
@@ -562,21 +429,12 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
           if (MODE == kModeAdjGrad)
             gn = vfma(vmul(vsplat<V>(a.neg_inv_dt2), vld<V>(T + 3 * TT + ti)), vfma(sv, dd, bl),
                       vld<V>(T + 4 * TT + ti));
-          if (yin[r] && live) {
+          if (yin[r] && live &&
+              WP_IN_BOUNDS(phys(z) >= 0 && phys(z) < a.g.nz && y0 + ty0 + r < a.g.ny && (!xin0 || gx < a.g.nx) &&
+                               (!xin1 || gx + 1 < a.g.nx) && gx >= 0,
+                           a.err)) {
             float *o = outp + po + rbase[r] + gx;
             float *gp = a.grad + po + rbase[r] + gx;
-            if constexpr (MODE == kModePair) {
-              if (role == 0) {  // q^n injected at its targets, as the injection kernel does
-                const int gy = y0 + ty0 + r;
-                for (int k = 0; k < ntgt_col; ++k) {
-                  const float4 e = tgt[k];
-                  if (__float_as_int(e.x) != phys(z) || __float_as_int(e.y) != gy) continue;
-                  const int tx_ = __float_as_int(e.z);
-                  if (tx_ == gx) un.x = __fadd_rn(un.x, e.w);
-                  if (NX == 2 && tx_ == gx + 1) un.y = __fadd_rn(un.y, e.w);
-                }
-              }
-            }
             if constexpr (NX == 2) {
               if (xin1) {
                 *reinterpret_cast<float2 *>(o) = un;
@@ -603,20 +461,6 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
 #pragma unroll
         for (int j = 0; j < 2 * R; ++j) q[r][j] = q[r][j + n];
     };
-    // kModePair, role 0: publish the planes of this column written so far
-    auto publish = [&](int zdone) {
-      if constexpr (MODE == kModePair) {
-        if (role == 0 && (((zdone - z0) & 3) == 0 || zdone == z1)) {  // every four planes and at the end
-          __threadfence();
-          asm volatile("bar.sync 1, %0;" ::"n"(kConsumerWarps * 32) : "memory");
-          if (warp == 0 && lane == 0) {
-            unsigned *f = a.progress + item;
-            const unsigned v = static_cast<unsigned>(zdone - z0);
-            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(f), "r"(v) : "memory");
-          }
-        }
-      }
-    };
     int z = z0;
     for (; z + C::ZU <= z1; z += C::ZU) {
       plane(z, std::integral_constant<int, 0>{});
@@ -624,12 +468,10 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
       if constexpr (C::ZU > 2) plane(z + 2, std::integral_constant<int, 2>{});
       if constexpr (C::ZU > 3) plane(z + 3, std::integral_constant<int, 3>{});
       rotate(std::integral_constant<int, C::ZU>{});
-      publish(z + C::ZU);
     }
     for (; z < z1; ++z) {
       plane(z, std::integral_constant<int, 0>{});
       rotate(std::integral_constant<int, 1>{});
-      publish(z + 1);
     }
     ub += static_cast<uint32_t>(z1 + R - z0);
   }

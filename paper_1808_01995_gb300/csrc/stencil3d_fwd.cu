@@ -26,15 +26,12 @@ static cudaError_t prepare_t(int *smem_bytes, int *blocks_per_sm, int *tile_y) {
     case 2: return F<2>(__VA_ARGS__);       \
     case 3: return F<3>(__VA_ARGS__);       \
     case 4: return F<4>(__VA_ARGS__);       \
-    case 5: return F<5>(__VA_ARGS__);       \
-    case 6: return F<6>(__VA_ARGS__);       \
-    case 7: return F<7>(__VA_ARGS__);       \
-    case 8: return F<8>(__VA_ARGS__);       \
     default: return cudaErrorInvalidValue;  \
   }
 
 cudaError_t launch_stencil3d_fwd(int R, dim3 grid, cudaStream_t st, const CUtensorMap *maps,
                                   const Stencil3dArgs &a) {
+  if (R > 4) return launch_stencil3d_hi(R, kModeFwd, grid, st, maps, a);
   WP_DISPATCH(launch_t, grid, st, maps, a)
 }
 
@@ -49,11 +46,7 @@ int stencil3d_tile_x_fwd(int R) {
     case 2: return tile_x_t<2>();
     case 3: return tile_x_t<3>();
     case 4: return tile_x_t<4>();
-    case 5: return tile_x_t<5>();
-    case 6: return tile_x_t<6>();
-    case 7: return tile_x_t<7>();
-    case 8: return tile_x_t<8>();
-    default: return 32;
+    default: return stencil3d_hi_tile_x(R, kModeFwd);
   }
 }
 
@@ -68,15 +61,12 @@ int stencil3d_tile_y_fwd(int R) {
     case 2: return tile_y_t<2>();
     case 3: return tile_y_t<3>();
     case 4: return tile_y_t<4>();
-    case 5: return tile_y_t<5>();
-    case 6: return tile_y_t<6>();
-    case 7: return tile_y_t<7>();
-    case 8: return tile_y_t<8>();
-    default: return 16;
+    default: return stencil3d_hi_tile_y(R, kModeFwd);
   }
 }
 
 cudaError_t prepare_stencil3d_fwd(int R, int *smem_bytes, int *blocks_per_sm, int *tile_y) {
+  if (R > 4) return prepare_stencil3d_hi(R, kModeFwd, smem_bytes, blocks_per_sm, tile_y);
   WP_DISPATCH(prepare_t, smem_bytes, blocks_per_sm, tile_y)
 }
 

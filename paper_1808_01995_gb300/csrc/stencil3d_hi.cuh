@@ -1,0 +1,429 @@
+// K1 (3D) for space orders above 8 (half-order R = 5..8): the same update as
+// stencil3d_kernel (Eq. fdWE-abc solved for u^{n+1}, the order-k Laplacian of
+// Eq. fdSpace, and in adjoint+gradient mode the fused correlation of Eq. Grad),
+// with a memory layout made for the wide stencils.
+//
+// Differences from the kernel of orders up to 8:
+//   - The z register queue of a lane needs the centre value of plane z + R when
+//     plane z is computed.  Here that value comes from a centre-only tile
+//     (TX x TY, no halo) of plane z + R that travels in the pointwise tile ring
+//     with plane z's u^{n-1}, b, s tiles, so the halo'd plane ring only holds the
+//     planes in flight (NH slots) instead of R + 1 + P planes.  The planes above
+//     a chunk are therefore streamed as centre tiles, not halo'd planes.
+//   - Ring depths are powers of two and ring positions are plain counters, so a
+//     plane's slot and phase cost a mask and a shift.
+//   - The first 2R queue entries of a chunk (planes z0 - R .. z0 + R - 1) are
+//     read with plain loads, all issued together.
+// Lanes own two adjacent x points (packed FP32x2 arithmetic) in NY consecutive
+// rows, as in the lower-order kernel; the Laplacian is accumulated in x, y and z
+// partial sums.  Every wait is bounded (%globaltimer); a timeout sets the abort
+// flag, the producer lets its copies land, and the error word reports it.
+// The wait limit is a.wait_ns.
+#pragma once
+
+#include "stencil3d.cuh"
+
+namespace wp {
+
+#ifndef WP_HI_W
+#define WP_HI_W 12       // consumer warps
+#endif
+#ifndef WP_HI_NY
+#define WP_HI_NY 2       // rows per lane, forward
+#endif
+#ifndef WP_HI_NY_ADJ
+#define WP_HI_NY_ADJ 2   // rows per lane, adjoint+gradient
+#endif
+#ifndef WP_HI_NH
+#define WP_HI_NH 4       // halo'd plane ring depth (power of two)
+#endif
+#ifndef WP_HI_NT
+#define WP_HI_NT 4       // pointwise tile ring depth (power of two), forward
+#endif
+#ifndef WP_HI_NT_ADJ
+#define WP_HI_NT_ADJ 4   // the same, adjoint+gradient (six streams per slot)
+#endif
+#ifndef WP_HI_ZU
+#define WP_HI_ZU 4       // planes per unrolled z step
+#endif
+#ifndef WP_HI_SPLIT_REGS
+#define WP_HI_SPLIT_REGS 1  // producer warpgroup gives its registers to the consumer warpgroups (setmaxnreg)
+#endif
+#ifndef WP_HI_SCALAR
+#define WP_HI_SCALAR 0   // scalar FP32 arithmetic instead of packed pairs (a sweep option)
+#endif
+
+template <int R, int MODE>
+struct CfgHi {
+  static constexpr int W = WP_HI_W;
+  static constexpr int NX = 2;
+  static constexpr int NY = MODE == kModeAdjGrad ? WP_HI_NY_ADJ : WP_HI_NY;
+  static constexpr int TX = 32 * NX;
+  static constexpr int TY = W * NY;
+  static constexpr int TT = TX * TY;
+  static constexpr int RX = (R + 3) / 4 * 4;  // x halo rounded to 16 bytes
+  static constexpr int RE = (R + 1) / 2 * 2;  // x window half-width (even)
+  static constexpr int PW = TX + 2 * RX;
+  static constexpr int PH = TY + 2 * R;
+  static constexpr int NH = WP_HI_NH;
+  static constexpr int NT = MODE == kModeAdjGrad ? WP_HI_NT_ADJ : WP_HI_NT;
+  static constexpr int ZU = WP_HI_ZU;
+  // streams of a tile slot: u^{n-1}, b, s, centre of u^n at plane z + R [, u^j, g]
+  static constexpr int S_UM = 0, S_B = 1, S_S = 2, S_UC = 3, S_UJ = 4, S_G = 5;
+  static constexpr int NSTREAM = MODE == kModeAdjGrad ? 6 : 4;
+  static constexpr int HSLOT = ((PW * PH * 4 + 127) / 128) * 128;
+  static constexpr int TSLOT = TT * 4;
+  static constexpr int T_OFF = NH * HSLOT;
+  static constexpr int BAR_OFF = T_OFF + NT * NSTREAM * TSLOT;
+  static constexpr int SMEM = BAR_OFF + 2 * (NH + NT) * 8 + NT * 4 + 16;
+  // Without the register split: W consumer warps and one producer warp.  With it
+  // (W a multiple of 4): W/4 consumer warpgroups and one producer warpgroup whose
+  // first lane issues the copies; the producer warpgroup drops to DEC registers per
+  // thread and the consumers rise to INC, within the block's launch allocation
+  // (THREADS x LAUNCH_REGS, LAUNCH_REGS being what the launch bound lets ptxas use:
+  // 65536 / THREADS rounded down to 8 after rounding THREADS up to whole warpgroups).
+  static constexpr bool SPLIT_REGS = WP_HI_SPLIT_REGS != 0 && W % 4 == 0;
+  static constexpr int THREADS = SPLIT_REGS ? (W + 4) * 32 : (W + 1) * 32;
+  static constexpr int LAUNCH_REGS = (65536 / ((THREADS + 127) / 128 * 128)) / 8 * 8;
+  static constexpr int DEC = 40;
+  static constexpr int INC_RAW = (THREADS * LAUNCH_REGS - 128 * DEC) / (W * 32) / 8 * 8;
+  static constexpr int INC = INC_RAW > 248 ? 248 : INC_RAW;
+  static_assert(!SPLIT_REGS || W * 32 * INC + 128 * DEC <= THREADS * LAUNCH_REGS, "register split over the launch");
+  static_assert((NH & (NH - 1)) == 0 && (NT & (NT - 1)) == 0, "ring depths must be powers of two");
+  static_assert(TSLOT % 128 == 0, "tile slots must stay 128-byte aligned");
+  static_assert(RX >= RE, "x halo must cover the x window");
+};
+
+// tm: [0] u^n halo'd plane box, [1] u^{n-1}, [2] b, [3] s, [4] u^j, [5] g, [6] u^n (tile boxes)
+// ISO: the three axes have the same spacing (cx = cy = cz): one coefficient per
+// distance j multiplies the sum of the six neighbours at that distance.
+template <int R, int MODE, bool ISO>
+__global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
+    stencil3d_hi_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_um,
+                        const __grid_constant__ CUtensorMap tm_b, const __grid_constant__ CUtensorMap tm_s,
+                        const __grid_constant__ CUtensorMap tm_uj, const __grid_constant__ CUtensorMap tm_g,
+                        const __grid_constant__ CUtensorMap tm_uc, const Stencil3dArgs a) {
+  using C = CfgHi<R, MODE>;
+  constexpr int NX = C::NX, NY = C::NY, TX = C::TX, TY = C::TY, TT = C::TT, W = C::W;
+  using V = float2;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float *hring = reinterpret_cast<float *>(smem);
+  float *tring = reinterpret_cast<float *>(smem + C::T_OFF);  // [NT][NSTREAM][TT]
+  uint64_t *full_h = reinterpret_cast<uint64_t *>(smem + C::BAR_OFF);
+  uint64_t *empty_h = full_h + C::NH;
+  uint64_t *full_t = empty_h + C::NH;
+  uint64_t *empty_t = full_t + C::NT;
+  volatile int *sflag = reinterpret_cast<volatile int *>(empty_t + C::NT);  // [NT]: s loaded
+  volatile int *abort_flag = sflag + C::NT;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int i = 0; i < C::NH; ++i) {
+      mbar_init(&full_h[i], 1);
+      mbar_init(&empty_h[i], W);
+    }
+    for (int i = 0; i < C::NT; ++i) {
+      mbar_init(&full_t[i], 1);
+      mbar_init(&empty_t[i], W);
+    }
+    *abort_flag = 0;
+    mbar_init_fence();
+  }
+  __syncthreads();
+
+  const int ncta = static_cast<int>(gridDim.x);
+  const int cta = static_cast<int>(blockIdx.x);
+  auto item_geom = [&](int item, int &tx, int &ty, int &z0, int &z1) {
+    const int tile = item / a.nzc, zc = item - tile * a.nzc;
+    tx = tile % a.tiles_x;
+    ty = tile / a.tiles_x;
+    z0 = a.bz0 + zc * a.zchunk;
+    z1 = min(z0 + a.zchunk, a.bz1);
+  };
+
+  if (warp >= W) {
+    // ---------------- producer (one lane) ----------------
+    if constexpr (C::SPLIT_REGS) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(C::DEC) : "memory");
+    if (warp == W && lane == 0) {
+      prefetch_tensormap(&tm_u);
+      prefetch_tensormap(&tm_um);
+      prefetch_tensormap(&tm_b);
+      prefetch_tensormap(&tm_s);
+      prefetch_tensormap(&tm_uc);
+      if (MODE == kModeAdjGrad) {
+        prefetch_tensormap(&tm_uj);
+        prefetch_tensormap(&tm_g);
+      }
+      uint32_t ih = 0, it_ = 0;  // planes issued into each ring
+      bool ok = true;
+      auto aligned = [&](const float *dst, int x) -> bool {
+        if ((smem_u32(dst) & 127u) == 0 && (x & 3) == 0) return true;
+        atomicCAS(a.err, 0, static_cast<int>(kErrLaunch));
+        *abort_flag = 1;
+        ok = false;
+        return false;
+      };
+      for (int item = cta; item < a.nitems && ok; item += ncta) {
+        int tx, ty, z0, z1;
+        item_geom(item, tx, ty, z0, z1);
+        if (z0 >= z1) continue;
+        const int x0 = a.bx0 + tx * TX, y0 = a.by0 + ty * TY;
+        const int fx0 = x0 / kFlagTX, fx1 = min((x0 + TX - 1) / kFlagTX + 1, a.flag_tiles_x);
+        const int fy0 = y0 / kTileFlagTY, fy1 = min((y0 + TY - 1) / kTileFlagTY + 1, a.flag_tiles_y);
+        auto word = [&](int w) -> unsigned {
+          unsigned v = 0;
+          if (w >= 0 && w < a.nzw)
+            for (int fy = fy0; fy < fy1; ++fy)
+              for (int fx = fx0; fx < fx1; ++fx)
+                v |= __ldg(a.tbits + (static_cast<long long>(fy) * a.flag_tiles_x + fx) * a.nzw + w);
+          return v;
+        };
+        int wcur = z0 >> 5;
+        unsigned bits = word(wcur);
+        for (int z = z0; z < z1 && ok; ++z) {
+          if ((z >> 5) != wcur) {
+            wcur = z >> 5;
+            bits = word(wcur);
+          }
+          const bool d = (bits >> (z & 31)) & 1u;
+          // tile slot of plane z: u^{n-1}, b, [s], centre of plane z + R [, u^j, g]
+          {
+            const uint32_t slot = it_ & (C::NT - 1);
+            if (it_ >= C::NT && !mbar_wait_bounded(&empty_t[slot], ((it_ / C::NT) - 1) & 1, abort_flag, a.wait_ns)) {
+              ok = false;
+              break;
+            }
+            float *t = tring + slot * (C::NSTREAM * TT);
+            if (!aligned(t, x0)) break;
+            sflag[slot] = d ? 1 : 0;  // published by the arrive below (release) to the waiters (acquire)
+            const int n = (MODE == kModeAdjGrad ? 5 : 3) + (d ? 1 : 0);
+            mbar_arrive_expect_tx(&full_t[slot], n * C::TSLOT);
+            tma_load_3d(t + C::S_UM * TT, &tm_um, x0, y0, z, &full_t[slot]);
+            tma_load_3d(t + C::S_B * TT, &tm_b, x0, y0, z, &full_t[slot]);
+            if (d) tma_load_3d(t + C::S_S * TT, &tm_s, x0, y0, z, &full_t[slot]);
+            tma_load_3d(t + C::S_UC * TT, &tm_uc, x0, y0, z + R, &full_t[slot]);
+            if (MODE == kModeAdjGrad) {
+              tma_load_3d(t + C::S_UJ * TT, &tm_uj, x0, y0, z, &full_t[slot]);
+              tma_load_3d(t + C::S_G * TT, &tm_g, x0, y0, z, &full_t[slot]);
+            }
+            ++it_;
+          }
+          // halo'd plane z of u^n
+          {
+            const uint32_t slot = ih & (C::NH - 1);
+            if (ih >= C::NH && !mbar_wait_bounded(&empty_h[slot], ((ih / C::NH) - 1) & 1, abort_flag, a.wait_ns)) {
+              ok = false;
+              break;
+            }
+            float *dst = hring + slot * (C::HSLOT / 4);
+            if (!aligned(dst, x0 - C::RX)) break;
+            mbar_arrive_expect_tx(&full_h[slot], C::PW * C::PH * 4);
+            tma_load_3d(dst, &tm_u, x0 - C::RX, y0 - R, z, &full_h[slot]);
+            ++ih;
+          }
+        }
+      }
+      if (*abort_flag) {
+        // let issued copies land (bounded) before shared memory goes away
+        const uint64_t t0 = global_timer_ns();
+        for (uint32_t j = ih > C::NH ? ih - C::NH : 0; j < ih; ++j)
+          while (!mbar_try_wait(&full_h[j & (C::NH - 1)], (j / C::NH) & 1) && global_timer_ns() - t0 < kWaitLimitNs) {
+          }
+        for (uint32_t j = it_ > C::NT ? it_ - C::NT : 0; j < it_; ++j)
+          while (!mbar_try_wait(&full_t[j & (C::NT - 1)], (j / C::NT) & 1) && global_timer_ns() - t0 < kWaitLimitNs) {
+          }
+        atomicCAS(a.err, 0, static_cast<int>(kErrWaitFull));
+      }
+    }
+    return;
+  }
+
+  // ---------------- consumers ----------------
+  if constexpr (C::SPLIT_REGS) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(C::INC) : "memory");
+  const int ty0 = warp * NY;          // first tile row of this lane
+  const int cx0 = C::RX + NX * lane;  // this lane's first column in a halo'd plane row
+  uint32_t hpos = 0, tpos = 0;        // ring positions of the next plane
+  auto release = [&](uint64_t *bar) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bar);
+  };
+  const V nidt2 = make_float2(a.neg_inv_dt2, a.neg_inv_dt2);
+
+  for (int item = cta; item < a.nitems; item += ncta) {
+    int tx, ty, z0, z1;
+    item_geom(item, tx, ty, z0, z1);
+    if (z0 >= z1) continue;
+    const int gx = a.bx0 + tx * TX + NX * lane;
+    const int y0 = a.by0 + ty * TY;
+    const bool xin0 = gx < a.bx1;
+    const bool xin1 = gx + 1 < a.bx1;
+    bool yin[NY];
+    int rofs[NY];  // in-plane offset of this lane's point 0 in each row (row clamped inside the grid)
+#pragma unroll
+    for (int r = 0; r < NY; ++r) {
+      const int gy = y0 + ty0 + r;
+      yin[r] = gy < a.by1;
+      rofs[r] = min(gy, a.g.ny - 1) * a.g.pitch;
+    }
+    const int gxc0 = min(gx, a.g.nx - 1), gxc1 = min(gx + 1, a.g.nx - 1);
+
+    // z queue: q[r][o + j] = u^n at plane z - R + j (o = offset of the plane in an unrolled step);
+    // planes z0 - R .. z0 + R - 1 first, with plain loads
+    V q[NY][2 * R + C::ZU];
+#pragma unroll
+    for (int j = 0; j < 2 * R; ++j) {
+      const int p = z0 - R + j;
+      const bool pin = p >= 0 && p < a.g.nz;
+      const float *src = a.u + static_cast<long long>(pin ? p : 0) * a.g.plane;
+#pragma unroll
+      for (int r = 0; r < NY; ++r) {
+        const bool ok = pin && yin[r];
+        q[r][j] = make_float2(ok && xin0 ? __ldg(src + rofs[r] + gxc0) : 0.f,
+                              ok && xin1 ? __ldg(src + rofs[r] + gxc1) : 0.f);
+      }
+    }
+
+    auto plane = [&](int z, auto oc) {
+      constexpr int o = decltype(oc)::value;
+      // pointwise tiles of plane z (and the centre of plane z + R)
+      const uint32_t tslot = tpos & (C::NT - 1);
+      mbar_wait_bounded(&full_t[tslot], (tpos / C::NT) & 1, abort_flag, a.wait_ns);
+      ++tpos;
+      const float *T = tring + tslot * (C::NSTREAM * TT);
+#pragma unroll
+      for (int r = 0; r < NY; ++r) q[r][2 * R + o] = vld<V>(T + C::S_UC * TT + (ty0 + r) * TX + NX * lane);
+      // x / y neighbours from the halo'd plane z
+      const uint32_t hslot = hpos & (C::NH - 1);
+      mbar_wait_bounded(&full_h[hslot], (hpos / C::NH) & 1, abort_flag, a.wait_ns);
+      ++hpos;
+      const float *P = hring + hslot * (C::HSLOT / 4);
+      V lap[NY];
+      {
+        V col[NY + 2 * R];
+#pragma unroll
+        for (int i = 0; i < NY + 2 * R; ++i) col[i] = vld<V>(P + (ty0 + i) * C::PW + cx0);
+#pragma unroll
+        for (int r = 0; r < NY; ++r) {
+          const float *pc = P + (ty0 + r + R) * C::PW + cx0;
+          float2 w[C::RE + 1];
+#pragma unroll
+          for (int k = 0; k <= C::RE; ++k) w[k] = vld<float2>(pc - C::RE + 2 * k);
+          auto win = [&](int i) -> float { return (i & 1) ? w[i >> 1].y : w[i >> 1].x; };
+          auto xsum = [&](int j) -> float2 {
+            if ((j & 1) == 0) return __fadd2_rn(w[(C::RE + j) >> 1], w[(C::RE - j) >> 1]);
+            return make_float2(win(C::RE + j) + win(C::RE - j), win(C::RE + 1 + j) + win(C::RE + 1 - j));
+          };
+          auto ysum = [&](int j) -> V { return vadd(col[R + r + j], col[R + r - j]); };
+          auto zsum = [&](int j) -> V { return vadd(q[r][o + R + j], q[r][o + R - j]); };
+#if WP_HI_SCALAR
+          // two scalar chains per partial sum (coefficients as constant operands)
+          float l2[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            auto pick = [&](V v) -> float { return h ? v.y : v.x; };
+            auto xs = [&](int j) -> float { return win(C::RE + h + j) + win(C::RE + h - j); };
+            auto ys = [&](int j) -> float { return pick(col[R + r + j]) + pick(col[R + r - j]); };
+            auto zs = [&](int j) -> float { return pick(q[r][o + R + j]) + pick(q[r][o + R - j]); };
+            float lx = a.c.c0 * pick(q[r][o + R]);
+            float ly = a.c.cy[1] * ys(1);
+            float lz = a.c.cz[1] * zs(1);
+#pragma unroll
+            for (int j = 1; j <= R; ++j) {
+              lx = fmaf(a.c.cx[j], xs(j), lx);
+              if (j > 1) {
+                ly = fmaf(a.c.cy[j], ys(j), ly);
+                lz = fmaf(a.c.cz[j], zs(j), lz);
+              }
+            }
+            l2[h] = lx + (ly + lz);
+          }
+          lap[r] = make_float2(l2[0], l2[1]);
+#else
+          if constexpr (ISO) {
+            // two chains (odd and even distances) of the six-neighbour sums
+            auto nsum = [&](int j) -> V { return vadd(vadd(xsum(j), ysum(j)), zsum(j)); };
+            V la = vfma(a.c.px[1], nsum(1), vmul(a.c.p0, q[r][o + R]));
+            V lb = vmul(a.c.px[2], nsum(2));
+#pragma unroll
+            for (int j = 3; j <= R; ++j) {
+              if (j & 1)
+                la = vfma(a.c.px[j], nsum(j), la);
+              else
+                lb = vfma(a.c.px[j], nsum(j), lb);
+            }
+            lap[r] = vadd(la, lb);
+            continue;
+          }
+          // three partial sums (x, y, z) keep every chain of dependent FMAs at most R long
+          V lx = vmul(a.c.p0, q[r][o + R]);
+          V ly = vmul(a.c.py[1], ysum(1));
+          V lz = vmul(a.c.pz[1], zsum(1));
+#pragma unroll
+          for (int j = 1; j <= R; ++j) {
+            lx = vfma(a.c.px[j], xsum(j), lx);
+            if (j > 1) {
+              ly = vfma(a.c.py[j], ysum(j), ly);
+              lz = vfma(a.c.pz[j], zsum(j), lz);
+            }
+          }
+          lap[r] = vadd(lx, vadd(ly, lz));
+#endif
+        }
+      }
+      release(&empty_h[hslot]);
+
+      const bool d = sflag[tslot] != 0;
+      const long long po = static_cast<long long>(z) * a.g.plane;
+      const bool live = !*abort_flag;
+#pragma unroll
+      for (int r = 0; r < NY; ++r) {
+        const int ti = (ty0 + r) * TX + NX * lane;
+        const V c = q[r][o + R];
+        const V dd = vsub(c, vld<V>(T + C::S_UM * TT + ti));
+        const V sv = d ? vld<V>(T + C::S_S * TT + ti) : make_float2(0.f, 0.f);
+        const V bl = vmul(vld<V>(T + C::S_B * TT + ti), lap[r]);
+        const V un = vadd(vfma(sv, dd, vadd(c, dd)), bl);
+        V gn = make_float2(0.f, 0.f);
+        if (MODE == kModeAdjGrad)
+          gn = vfma(vmul(nidt2, vld<V>(T + C::S_UJ * TT + ti)), vfma(sv, dd, bl), vld<V>(T + C::S_G * TT + ti));
+        if (yin[r] && live &&
+            WP_IN_BOUNDS(z >= 0 && z < a.g.nz && y0 + ty0 + r < a.g.ny && (!xin0 || gx < a.g.nx) &&
+                             (!xin1 || gx + 1 < a.g.nx) && gx >= 0,
+                         a.err)) {
+          float *op = a.out + po + rofs[r] + gx;
+          float *gp = a.grad + po + rofs[r] + gx;
+          if (xin1) {
+            *reinterpret_cast<float2 *>(op) = un;
+            if (MODE == kModeAdjGrad) *reinterpret_cast<float2 *>(gp) = gn;
+          } else if (xin0) {
+            op[0] = un.x;
+            if (MODE == kModeAdjGrad) gp[0] = gn.x;
+          }
+        }
+      }
+      release(&empty_t[tslot]);
+    };
+    auto rotate = [&](auto nc) {
+      constexpr int n = decltype(nc)::value;
+#pragma unroll
+      for (int r = 0; r < NY; ++r)
+#pragma unroll
+        for (int j = 0; j < 2 * R; ++j) q[r][j] = q[r][j + n];
+    };
+    int z = z0;
+    for (; z + C::ZU <= z1; z += C::ZU) {
+      plane(z, std::integral_constant<int, 0>{});
+      if constexpr (C::ZU > 1) plane(z + 1, std::integral_constant<int, 1>{});
+      if constexpr (C::ZU > 2) plane(z + 2, std::integral_constant<int, 2>{});
+      if constexpr (C::ZU > 3) plane(z + 3, std::integral_constant<int, 3>{});
+      rotate(std::integral_constant<int, C::ZU>{});
+    }
+    for (; z < z1; ++z) {
+      plane(z, std::integral_constant<int, 0>{});
+      rotate(std::integral_constant<int, 1>{});
+    }
+  }
+}
+
+}  // namespace wp

@@ -13,11 +13,23 @@ namespace wp {
 // Device error codes written to the context's error word (first error wins).
 enum DeviceError : int {
   kErrNone = 0,
-  kErrWaitFull = 1,   // a TMA completion barrier did not complete in time
+  kErrWaitFull = 1,   // a wait on a ring barrier gave up (its limit ran out)
   kErrLaunch = 2,     // a kernel was launched with an unsupported shape
+  kErrBounds = 4,     // debug builds: an index outside its array, or a nonzero pitch padding value
 };
 
-// A wait gives up after this many nanoseconds of %globaltimer.
+// Debug builds (-DWP_DEBUG_BOUNDS): WP_IN_BOUNDS(cond, err) records kErrBounds in
+// the error word and is false when cond fails, so that the access it guards is
+// skipped; release builds compile it to `true`.
+#ifdef WP_DEBUG_BOUNDS
+#define WP_IN_BOUNDS(cond, err) ((cond) ? true : (atomicCAS((err), 0, static_cast<int>(::wp::kErrBounds)), false))
+#else
+#define WP_IN_BOUNDS(cond, err) true
+#endif
+
+// Default limit of a wait, in nanoseconds of %globaltimer (kernels take theirs
+// from an argument; a context may set another one).  Letting copies that were
+// already issued land before a CTA exits always uses this limit.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -61,6 +73,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
+// try_wait with a suspend-time hint: a thread whose phase is not complete may
+// sleep up to hint_ns (it wakes when the phase completes) instead of returning
+// after the system-dependent limit, so waiting warps leave the issue slots to
+// the computing ones.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
+#ifndef WP_WAIT_HINT_NS
+#define WP_WAIT_HINT_NS 0  // suspend-time hint of the bounded waits (0: the system's own limit)
+#endif
+
 // Non-blocking probe of phase `parity` of `bar` (try_wait may suspend the thread
 // for a while when the phase is not complete; test_wait returns at once).
 __device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
@@ -75,15 +107,30 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for phase `parity` of `bar`; false (and *abort set) after the time limit
-// or when another thread of the block has already aborted.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
-  if (mbar_try_wait(bar, parity)) return true;
+// Wait for phase `parity` of `bar`; false (and *abort set) once limit_ns has
+// passed, or when another thread of the block has already aborted.  With
+// limit_ns = 0 a phase that is not complete at the first look gives up at once.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                                  uint64_t limit_ns) {
+  if (limit_ns == 0) {
+    if (mbar_test_wait(bar, parity)) return true;
+    *abort_flag = 1;
+    return false;
+  }
+  auto try_once = [&]() -> bool {
+    if constexpr (WP_WAIT_HINT_NS > 0) {
+      const uint32_t hint = static_cast<uint32_t>(limit_ns < WP_WAIT_HINT_NS ? limit_ns : WP_WAIT_HINT_NS);
+      return mbar_try_wait_hint(bar, parity, hint);
+    } else {
+      return mbar_try_wait(bar, parity);
+    }
+  };
+  if (try_once()) return true;
   const uint64_t t0 = global_timer_ns();
   while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (try_once()) return true;
     if (*abort_flag) return false;
-    if (global_timer_ns() - t0 > kWaitLimitNs) {
+    if (global_timer_ns() - t0 > limit_ns) {
       *abort_flag = 1;
       return false;
     }
@@ -112,6 +159,11 @@ struct LapCoef {
   float cz[9];
   float cy[9];
   float cx[9];
+  // the same coefficients as packed pairs (c, c), operands of FP32x2 arithmetic
+  float2 p0;
+  float2 pz[9];
+  float2 py[9];
+  float2 px[9];
 };
 
 // Geometry of a pitched field: element (z, y, x) at z*plane + y*pitch + x.

@@ -69,8 +69,36 @@ def estimate_bytes(req: ShotRequest) -> int:
     return W.wp_estimate_bytes(req.grid, len(req.src), len(req.rec), mode, req.snap_interval)
 
 
+class _NvtxRange:
+    """NVTX range "serve.<kind>" around one request (torch's NVTX binding; a no-op
+    without it)."""
+
+    def __init__(self, name: str):
+        self.name = name
+        self.pushed = False
+
+    def __enter__(self):
+        try:
+            import torch
+            torch.cuda.nvtx.range_push(self.name)
+            self.pushed = True
+        except Exception:
+            pass
+        return self
+
+    def __exit__(self, *exc):
+        if self.pushed:
+            import torch
+            torch.cuda.nvtx.range_pop()
+
+
 def run_request(ctx_handle: int, req: ShotRequest):
     """Execute one request through the C ABI on a context (host arrays)."""
+    with _NvtxRange(f"serve.{req.kind}"):
+        return _run_request(ctx_handle, req)
+
+
+def _run_request(ctx_handle: int, req: ShotRequest):
     if req.kind == "forward":
         return W.wp_forward(ctx_handle, req.grid, req.m, req.eta, req.wavelet, req.src, req.rec), None
     if req.kind == "gradient":
@@ -281,25 +309,37 @@ def serve_stream(requests: list[ShotRequest], arrivals, slots: int = 4, hbm_budg
                                                 "budget_bytes": server.budget})
 
 
-def serve_sequential_plain(requests: list[ShotRequest], arrivals, device: int = 0) -> dict:
-    """The same stream served one request at a time, each with a fresh context
-    (nothing resident between requests, no overlap)."""
+def serve_sequential_plain(requests: list[ShotRequest], arrivals, device: int = 0,
+                           reuse_context: bool = False) -> dict:
+    """The same stream served one request at a time, in arrival order, with no
+    overlap.  By default each request gets a fresh context (nothing resident
+    between requests: the plain one-call-per-shot baseline); with reuse_context
+    one context serves them all, so its device pool and kernels stay warm and the
+    only thing missing against the server is the overlap of requests."""
     t0 = time.perf_counter()
-    for req, t in zip(requests, arrivals):
-        now = time.perf_counter() - t0
-        if t > now:
-            time.sleep(t - now)
-        req.arrival = float(t)
-        req.t_admit = time.perf_counter() - t0
-        try:
-            with W.Context(device) as c:
-                req.result, req.misfit = run_request(c.handle, req)
-            req.status = "done"
-        except W.WpError as e:
-            req.status, req.error, req.error_status = "error", str(e), e.status
-        req.t_done = time.perf_counter() - t0
+    shared = W.Context(device) if reuse_context else None
+    try:
+        for req, t in zip(requests, arrivals):
+            now = time.perf_counter() - t0
+            if t > now:
+                time.sleep(t - now)
+            req.arrival = float(t)
+            req.t_admit = time.perf_counter() - t0
+            try:
+                if shared is not None:
+                    req.result, req.misfit = run_request(shared.handle, req)
+                else:
+                    with W.Context(device) as c:
+                        req.result, req.misfit = run_request(c.handle, req)
+                req.status = "done"
+            except W.WpError as e:
+                req.status, req.error, req.error_status = "error", str(e), e.status
+            req.t_done = time.perf_counter() - t0
+    finally:
+        if shared is not None:
+            shared.close()
     makespan = time.perf_counter() - t0
-    return summarize(requests, makespan, extra={"slots": 1})
+    return summarize(requests, makespan, extra={"slots": 1, "context": "reused" if reuse_context else "fresh"})
 
 
 def summarize(requests: list[ShotRequest], makespan: float, extra: dict | None = None) -> dict:

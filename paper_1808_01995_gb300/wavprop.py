@@ -17,7 +17,9 @@ from dataclasses import dataclass
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libwavprop.so")
+# WAVPROP_LIB selects another build of the library (e.g. one compiled with the
+# device bounds checks); the default is the in-tree libwavprop.so.
+LIB_PATH = os.environ.get("WAVPROP_LIB") or os.path.join(HERE, "libwavprop.so")
 
 WP_OK, WP_EINVAL, WP_ECFL, WP_ENOMEM, WP_ENONFINITE, WP_ECUDA, WP_ETIMEOUT, WP_EDEVICE = 0, -1, -2, -3, -4, -5, -6, -7
 WP_BUDGET_AUTO = ctypes.c_size_t(-1).value
@@ -31,9 +33,9 @@ EXPORTED = [
     "wp_bytes_in_use", "wp_kernel_launches", "wp_set_profiling", "wp_profile_read",
     "wp_fwi_gradient", "wp_fwi_gradient_dev", "wp_trim", "wp_set_budget", "wp_axpy_dev",
     "wp_update_model_dev", "wp_gradient_checkpointed", "wp_gradient_checkpointed_dev", "wp_checkpoint_schedule",
-    "wp_gradient_reconstruct", "wp_gradient_reconstruct_dev", "wp_set_temporal_blocking",
+    "wp_gradient_reconstruct", "wp_gradient_reconstruct_dev", "wp_set_wait_limit",
     "wp_convection_2d", "wp_convection_2d_dev", "wp_burgers_2d", "wp_burgers_2d_dev", "wp_poisson_2d",
-    "wp_poisson_2d_dev",
+    "wp_poisson_2d_dev", "wp_misfit_dev",
 ]
 
 
@@ -133,7 +135,7 @@ def lib() -> ctypes.CDLL:
         "wp_axpy_dev": ([_vp, ctypes.c_longlong, ctypes.c_float, _fp, _fp, _vp], _i),
         "wp_gradient_checkpointed": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _fp, _i, _dp, _i, _fp], _i),
         "wp_gradient_checkpointed_dev": ([_vp, _gp, _fp, _fp, _fp, _i, _dp, _fp, _i, _dp, _i, _fp, _vp], _i),
-        "wp_set_temporal_blocking": ([_vp, _i], _i),
+        "wp_set_wait_limit": ([_vp, ctypes.c_double], _i),
         "wp_convection_2d": ([_vp, _i, _i, _d, _d, _d, _d, _i, _fp, _fp], _i),
         "wp_convection_2d_dev": ([_vp, _i, _i, _d, _d, _d, _d, _i, _fp, _fp, _vp], _i),
         "wp_burgers_2d": ([_vp, _i, _i, _d, _d, _d, _d, _i, _fp, _fp, _fp, _fp], _i),
@@ -145,6 +147,7 @@ def lib() -> ctypes.CDLL:
         "wp_checkpoint_schedule": ([_i, _i, _vp, _i, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_longlong)], _i),
         "wp_update_model_dev": ([_vp, ctypes.c_longlong, ctypes.c_float, _fp, _fp, ctypes.c_float, ctypes.c_float,
                                  _vp], _i),
+        "wp_misfit_dev": ([_vp, ctypes.c_longlong, _fp, _fp, _fp, ctypes.POINTER(ctypes.c_double), _vp], _i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -182,11 +185,35 @@ def _ptr(a):
     return a.data_ptr() if a.numel() else None
 
 
-def _dev_f32(t, what):
+def _dev_f32(t, what, numel=None, device=None):
+    """A contiguous float32 CUDA tensor of `numel` values on `device` (checked
+    before the library sees the pointer: a host array, a short buffer or a tensor
+    on another GPU would be read or written by every kernel of the call)."""
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
         raise TypeError(f"{what} must be a contiguous float32 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{what} holds {t.numel()} values, {numel} expected")
+    if device is not None and t.device != device:
+        raise ValueError(f"{what} is on {t.device}, the other arrays of the call on {device}")
     return t
+
+
+def _dev_opt(t, what, numel, device):
+    """As _dev_f32, for an array the call only touches when numel > 0 (None allowed then)."""
+    if numel == 0 and (t is None or getattr(t, "numel", lambda: 1)() == 0):
+        return None
+    if t is None:
+        raise ValueError(f"{what} is required ({numel} values)")
+    return _dev_f32(t, what, numel, device)
+
+
+def _fields(grid, m, eta):
+    """m and eta checked against the grid; returns (m, eta, device)."""
+    n = int(np.prod(grid.shape))
+    _dev_f32(m, "m", n)
+    _dev_f32(eta, "eta", n, m.device)
+    return m, eta, m.device
 
 
 def _stream(stream):
@@ -312,35 +339,45 @@ def wp_gradient(ctx: int, grid: Grid, m, eta, wavelet, src, residual, rec, snap_
 def wp_forward_dev(ctx: int, grid: Grid, m, eta, wavelet, src, rec, rec_out, stream=None) -> None:
     src = _coords(src, grid.ndim)
     rec = _coords(rec, grid.ndim)
+    m, eta, dev = _fields(grid, m, eta)
+    wavelet = _dev_opt(wavelet, "wavelet", grid.nt * len(src), dev)
+    rec_out = _dev_opt(rec_out, "rec_out", grid.nt * len(rec), dev)
     g = grid.c()
-    _check(lib().wp_forward_dev(ctx, ctypes.byref(g), _ptr(_dev_f32(m, "m")), _ptr(_dev_f32(eta, "eta")),
-                                _ptr(wavelet), len(src), _ptr(src), len(rec), _ptr(rec), _ptr(rec_out),
-                                _stream(stream)))
+    _check(lib().wp_forward_dev(ctx, ctypes.byref(g), _ptr(m), _ptr(eta), _ptr(wavelet), len(src), _ptr(src),
+                                len(rec), _ptr(rec), _ptr(rec_out), _stream(stream)))
 
 
 def wp_adjoint_dev(ctx: int, grid: Grid, m, eta, rec_data, rec, src, src_out, stream=None) -> None:
     src = _coords(src, grid.ndim)
     rec = _coords(rec, grid.ndim)
+    m, eta, dev = _fields(grid, m, eta)
+    rec_data = _dev_opt(rec_data, "rec_data", grid.nt * len(rec), dev)
+    src_out = _dev_opt(src_out, "src_out", grid.nt * len(src), dev)
     g = grid.c()
-    _check(lib().wp_adjoint_dev(ctx, ctypes.byref(g), _ptr(_dev_f32(m, "m")), _ptr(_dev_f32(eta, "eta")),
-                                _ptr(rec_data), len(rec), _ptr(rec), len(src), _ptr(src), _ptr(src_out),
-                                _stream(stream)))
+    _check(lib().wp_adjoint_dev(ctx, ctypes.byref(g), _ptr(m), _ptr(eta), _ptr(rec_data), len(rec), _ptr(rec),
+                                len(src), _ptr(src), _ptr(src_out), _stream(stream)))
 
 
 def wp_gradient_dev(ctx: int, grid: Grid, m, eta, wavelet, src, residual, rec, snap_interval, grad_out,
                     stream=None) -> None:
     src = _coords(src, grid.ndim)
     rec = _coords(rec, grid.ndim)
+    m, eta, dev = _fields(grid, m, eta)
+    wavelet = _dev_opt(wavelet, "wavelet", grid.nt * len(src), dev)
+    residual = _dev_opt(residual, "residual", grid.nt * len(rec), dev)
+    _dev_f32(grad_out, "grad_out", m.numel(), dev)
     g = grid.c()
-    _check(lib().wp_gradient_dev(ctx, ctypes.byref(g), _ptr(_dev_f32(m, "m")), _ptr(_dev_f32(eta, "eta")),
-                                 _ptr(wavelet), len(src), _ptr(src), _ptr(residual), len(rec), _ptr(rec),
-                                 int(snap_interval), _ptr(_dev_f32(grad_out, "grad_out")), _stream(stream)))
+    _check(lib().wp_gradient_dev(ctx, ctypes.byref(g), _ptr(m), _ptr(eta), _ptr(wavelet), len(src), _ptr(src),
+                                 _ptr(residual), len(rec), _ptr(rec), int(snap_interval), _ptr(grad_out),
+                                 _stream(stream)))
 
 
 def wp_propagate_dev(ctx: int, grid: Grid, m, eta, u_prev, u, nsteps: int, stream=None) -> None:
+    m, eta, dev = _fields(grid, m, eta)
+    _dev_f32(u_prev, "u_prev", m.numel(), dev)
+    _dev_f32(u, "u", m.numel(), dev)
     g = grid.c()
-    _check(lib().wp_propagate_dev(ctx, ctypes.byref(g), _ptr(_dev_f32(m, "m")), _ptr(_dev_f32(eta, "eta")),
-                                  _ptr(_dev_f32(u_prev, "u_prev")), _ptr(_dev_f32(u, "u")), int(nsteps),
+    _check(lib().wp_propagate_dev(ctx, ctypes.byref(g), _ptr(m), _ptr(eta), _ptr(u_prev), _ptr(u), int(nsteps),
                                   _stream(stream)))
 
 
@@ -348,16 +385,25 @@ def wp_forward_save(ctx: int, grid: Grid, m, eta, wavelet, src, rec, snap_interv
                     stream=None) -> int:
     src = _coords(src, grid.ndim)
     rec = _coords(rec, grid.ndim)
+    m, eta, dev = _fields(grid, m, eta)
+    wavelet = _dev_opt(wavelet, "wavelet", grid.nt * len(src), dev)
+    if rec_out is not None:
+        rec_out = _dev_opt(rec_out, "rec_out", grid.nt * len(rec), dev)
     g = grid.c()
     st = _vp()
-    _check(lib().wp_forward_save(ctx, ctypes.byref(g), _ptr(_dev_f32(m, "m")), _ptr(_dev_f32(eta, "eta")),
-                                 _ptr(wavelet), len(src), _ptr(src), len(rec), _ptr(rec), int(snap_interval),
-                                 _ptr(rec_out), _stream(stream), ctypes.byref(st)))
+    _check(lib().wp_forward_save(ctx, ctypes.byref(g), _ptr(m), _ptr(eta), _ptr(wavelet), len(src), _ptr(src),
+                                 len(rec), _ptr(rec), int(snap_interval), _ptr(rec_out), _stream(stream),
+                                 ctypes.byref(st)))
     return st.value
 
 
 def wp_backward(state: int, residual, grad_out, stream=None) -> None:
-    _check(lib().wp_backward(state, _ptr(residual), _ptr(_dev_f32(grad_out, "grad_out")), _stream(stream)))
+    """The state's own sizes are checked by the library; here the arrays must be
+    float32 CUDA tensors on one device."""
+    _dev_f32(grad_out, "grad_out")
+    if residual is not None:
+        _dev_f32(residual, "residual", None, grad_out.device)
+    _check(lib().wp_backward(state, _ptr(residual), _ptr(grad_out), _stream(stream)))
 
 
 def wp_fwi_gradient(ctx: int, grid: Grid, m, eta, wavelet, src, d_obs, rec, snap_interval: int):
@@ -380,12 +426,15 @@ def wp_fwi_gradient_dev(ctx: int, grid: Grid, m, eta, wavelet, src, d_obs, rec, 
                         stream=None) -> float:
     src = _coords(src, grid.ndim)
     rec = _coords(rec, grid.ndim)
+    m, eta, dev = _fields(grid, m, eta)
+    wavelet = _dev_opt(wavelet, "wavelet", grid.nt * len(src), dev)
+    d_obs = _dev_opt(d_obs, "d_obs", grid.nt * len(rec), dev)
+    _dev_f32(grad_out, "grad_out", m.numel(), dev)
     g = grid.c()
     J = ctypes.c_double()
-    _check(lib().wp_fwi_gradient_dev(ctx, ctypes.byref(g), _ptr(_dev_f32(m, "m")), _ptr(_dev_f32(eta, "eta")),
-                                     _ptr(wavelet), len(src), _ptr(src), _ptr(d_obs), len(rec), _ptr(rec),
-                                     int(snap_interval), _ptr(_dev_f32(grad_out, "grad_out")), ctypes.byref(J),
-                                     _stream(stream)))
+    _check(lib().wp_fwi_gradient_dev(ctx, ctypes.byref(g), _ptr(m), _ptr(eta), _ptr(wavelet), len(src), _ptr(src),
+                                     _ptr(d_obs), len(rec), _ptr(rec), int(snap_interval), _ptr(grad_out),
+                                     ctypes.byref(J), _stream(stream)))
     return J.value
 
 
@@ -409,11 +458,14 @@ def wp_gradient_checkpointed_dev(ctx: int, grid: Grid, m, eta, wavelet, src, res
                                  grad_out, stream=None) -> None:
     src = _coords(src, grid.ndim)
     rec = _coords(rec, grid.ndim)
+    m, eta, dev = _fields(grid, m, eta)
+    wavelet = _dev_opt(wavelet, "wavelet", grid.nt * len(src), dev)
+    residual = _dev_opt(residual, "residual", grid.nt * len(rec), dev)
+    _dev_f32(grad_out, "grad_out", m.numel(), dev)
     g = grid.c()
-    _check(lib().wp_gradient_checkpointed_dev(ctx, ctypes.byref(g), _ptr(_dev_f32(m, "m")),
-                                              _ptr(_dev_f32(eta, "eta")), _ptr(wavelet), len(src), _ptr(src),
-                                              _ptr(residual), len(rec), _ptr(rec), int(checkpoints),
-                                              _ptr(_dev_f32(grad_out, "grad_out")), _stream(stream)))
+    _check(lib().wp_gradient_checkpointed_dev(ctx, ctypes.byref(g), _ptr(m), _ptr(eta), _ptr(wavelet), len(src),
+                                              _ptr(src), _ptr(residual), len(rec), _ptr(rec), int(checkpoints),
+                                              _ptr(grad_out), _stream(stream)))
 
 
 def wp_gradient_reconstruct(ctx: int, grid: Grid, m, eta, wavelet, src, residual, rec) -> np.ndarray:
@@ -435,11 +487,14 @@ def wp_gradient_reconstruct_dev(ctx: int, grid: Grid, m, eta, wavelet, src, resi
                                 stream=None) -> None:
     src = _coords(src, grid.ndim)
     rec = _coords(rec, grid.ndim)
+    m, eta, dev = _fields(grid, m, eta)
+    wavelet = _dev_opt(wavelet, "wavelet", grid.nt * len(src), dev)
+    residual = _dev_opt(residual, "residual", grid.nt * len(rec), dev)
+    _dev_f32(grad_out, "grad_out", m.numel(), dev)
     g = grid.c()
-    _check(lib().wp_gradient_reconstruct_dev(ctx, ctypes.byref(g), _ptr(_dev_f32(m, "m")),
-                                             _ptr(_dev_f32(eta, "eta")), _ptr(wavelet), len(src), _ptr(src),
-                                             _ptr(residual), len(rec), _ptr(rec),
-                                             _ptr(_dev_f32(grad_out, "grad_out")), _stream(stream)))
+    _check(lib().wp_gradient_reconstruct_dev(ctx, ctypes.byref(g), _ptr(m), _ptr(eta), _ptr(wavelet), len(src),
+                                             _ptr(src), _ptr(residual), len(rec), _ptr(rec), _ptr(grad_out),
+                                             _stream(stream)))
 
 
 def wp_checkpoint_schedule(nt: int, checkpoints: int):
@@ -453,9 +508,9 @@ def wp_checkpoint_schedule(nt: int, checkpoints: int):
     return ops, int(fw.value)
 
 
-def wp_set_temporal_blocking(ctx: int, mode) -> None:
-    """0: single steps; 1 (or True): two steps per launch on chip; 2: two CTA roles."""
-    _check(lib().wp_set_temporal_blocking(ctx, int(mode)))
+def wp_set_wait_limit(ctx: int, seconds: float) -> None:
+    """Limit of the stencil kernels' internal waits (default 2 s; 0: give up unless complete)."""
+    _check(lib().wp_set_wait_limit(ctx, float(seconds)))
 
 
 # ---------------------------------------------------------------------------
@@ -478,8 +533,9 @@ def wp_convection_2d(ctx: int, u0, dx: float, dy: float, dt: float, c: float, nt
 
 def wp_convection_2d_dev(ctx: int, u0, dx, dy, dt, c, nt, u_out, stream=None) -> None:
     ny, nx = u0.shape
-    _check(lib().wp_convection_2d_dev(ctx, nx, ny, dx, dy, dt, c, int(nt), _ptr(_dev_f32(u0, "u0")),
-                                      _ptr(_dev_f32(u_out, "u_out")), _stream(stream)))
+    _dev_f32(u0, "u0")
+    _dev_f32(u_out, "u_out", u0.numel(), u0.device)
+    _check(lib().wp_convection_2d_dev(ctx, nx, ny, dx, dy, dt, c, int(nt), _ptr(u0), _ptr(u_out), _stream(stream)))
 
 
 def wp_burgers_2d(ctx: int, u0, v0, dx: float, dy: float, dt: float, nu: float, nt: int):
@@ -494,9 +550,11 @@ def wp_burgers_2d(ctx: int, u0, v0, dx: float, dy: float, dt: float, nu: float, 
 
 def wp_burgers_2d_dev(ctx: int, u0, v0, dx, dy, dt, nu, nt, u_out, v_out, stream=None) -> None:
     ny, nx = u0.shape
-    _check(lib().wp_burgers_2d_dev(ctx, nx, ny, dx, dy, dt, nu, int(nt), _ptr(_dev_f32(u0, "u0")),
-                                   _ptr(_dev_f32(v0, "v0")), _ptr(_dev_f32(u_out, "u_out")),
-                                   _ptr(_dev_f32(v_out, "v_out")), _stream(stream)))
+    _dev_f32(u0, "u0")
+    for t, what in ((v0, "v0"), (u_out, "u_out"), (v_out, "v_out")):
+        _dev_f32(t, what, u0.numel(), u0.device)
+    _check(lib().wp_burgers_2d_dev(ctx, nx, ny, dx, dy, dt, nu, int(nt), _ptr(u0), _ptr(v0), _ptr(u_out),
+                                   _ptr(v_out), _stream(stream)))
 
 
 def wp_poisson_2d(ctx: int, p0, b, dx: float, dy: float, nit: int) -> np.ndarray:
@@ -511,8 +569,10 @@ def wp_poisson_2d(ctx: int, p0, b, dx: float, dy: float, nit: int) -> np.ndarray
 
 def wp_poisson_2d_dev(ctx: int, p0, b, dx, dy, nit, p_out, stream=None) -> None:
     ny, nx = p0.shape
-    _check(lib().wp_poisson_2d_dev(ctx, nx, ny, dx, dy, int(nit), _ptr(_dev_f32(p0, "p0")), _ptr(_dev_f32(b, "b")),
-                                   _ptr(_dev_f32(p_out, "p_out")), _stream(stream)))
+    _dev_f32(p0, "p0")
+    _dev_f32(b, "b", p0.numel(), p0.device)
+    _dev_f32(p_out, "p_out", p0.numel(), p0.device)
+    _check(lib().wp_poisson_2d_dev(ctx, nx, ny, dx, dy, int(nit), _ptr(p0), _ptr(b), _ptr(p_out), _stream(stream)))
 
 
 def wp_trim(ctx: int, keep_bytes: int = 0) -> None:
@@ -521,18 +581,28 @@ def wp_trim(ctx: int, keep_bytes: int = 0) -> None:
 
 def wp_axpy_dev(ctx: int, alpha: float, x, y, stream=None) -> None:
     """y += alpha x (contiguous float32 CUDA tensors of equal size)."""
-    if x.numel() != y.numel():
-        raise ValueError("x and y differ in size")
-    _check(lib().wp_axpy_dev(ctx, int(y.numel()), float(alpha), _ptr(_dev_f32(x, "x")), _ptr(_dev_f32(y, "y")),
-                             _stream(stream)))
+    _dev_f32(y, "y")
+    _dev_f32(x, "x", y.numel(), y.device)
+    _check(lib().wp_axpy_dev(ctx, int(y.numel()), float(alpha), _ptr(x), _ptr(y), _stream(stream)))
+
+
+def wp_misfit_dev(ctx: int, d, d_obs, r_out, stream=None) -> float:
+    """r_out = d - d_obs and J = 1/2 ||d - d_obs||^2 (contiguous float32 CUDA tensors of one size)."""
+    _dev_f32(d, "d")
+    _dev_f32(d_obs, "d_obs", d.numel(), d.device)
+    _dev_f32(r_out, "r_out", d.numel(), d.device)
+    J = ctypes.c_double()
+    _check(lib().wp_misfit_dev(ctx, int(d.numel()), _ptr(d), _ptr(d_obs), _ptr(r_out), ctypes.byref(J),
+                               _stream(stream)))
+    return J.value
 
 
 def wp_update_model_dev(ctx: int, step: float, grad, m, m_min: float, m_max: float, stream=None) -> None:
     """m = clamp(m - step grad, m_min, m_max) in place."""
-    if grad.numel() != m.numel():
-        raise ValueError("grad and m differ in size")
-    _check(lib().wp_update_model_dev(ctx, int(m.numel()), float(step), _ptr(_dev_f32(grad, "grad")),
-                                     _ptr(_dev_f32(m, "m")), float(m_min), float(m_max), _stream(stream)))
+    _dev_f32(m, "m")
+    _dev_f32(grad, "grad", m.numel(), m.device)
+    _check(lib().wp_update_model_dev(ctx, int(m.numel()), float(step), _ptr(grad), _ptr(m), float(m_min),
+                                     float(m_max), _stream(stream)))
 
 
 def wp_set_budget(ctx: int, hbm_budget_bytes: int) -> None:
@@ -552,10 +622,12 @@ def wp_forward_noalloc(grid: Grid, m, eta, wavelet, src, rec, rec_out, stream=No
     every call (serialise calls; they race if they overlap on the GPU)."""
     src = _coords(src, grid.ndim)
     rec = _coords(rec, grid.ndim)
+    m, eta, dev = _fields(grid, m, eta)
+    wavelet = _dev_opt(wavelet, "wavelet", grid.nt * len(src), dev)
+    rec_out = _dev_opt(rec_out, "rec_out", grid.nt * len(rec), dev)
     g = grid.c()
-    _check(lib().wp_forward_noalloc(ctypes.byref(g), _ptr(_dev_f32(m, "m")), _ptr(_dev_f32(eta, "eta")),
-                                    _ptr(wavelet), len(src), _ptr(src), len(rec), _ptr(rec), _ptr(rec_out),
-                                    _stream(stream)))
+    _check(lib().wp_forward_noalloc(ctypes.byref(g), _ptr(m), _ptr(eta), _ptr(wavelet), len(src), _ptr(src),
+                                    len(rec), _ptr(rec), _ptr(rec_out), _stream(stream)))
 
 
 class Context:
