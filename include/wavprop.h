@@ -250,9 +250,10 @@ int wp_set_budget(wp_ctx *ctx, size_t hbm_budget_bytes);
  * resident in *state; wp_backward(state, residual, grad) then returns
  * J^T residual = dJ/dm for J = 1/2 ||d - d_obs||^2 with residual = d - d_obs
  * (or any upstream gradient dL/dd).  A state may be back-propagated more than
- * once; wp_state_free releases its memory.  The state borrows ctx: free it
- * before wp_destroy(ctx), and do not use ctx for another call in between if
- * memory is tight (the state's memory counts against ctx's budget). */
+ * once; wp_state_free releases its memory.  The state borrows ctx (its memory
+ * counts against ctx's budget).  If ctx is destroyed first, wp_destroy releases
+ * the state's device memory and detaches it: wp_backward on it then returns
+ * WP_EINVAL, and wp_state_free only frees the handle. */
 int wp_forward_save(wp_ctx *ctx, const wp_grid *grid, const float *m, const float *eta,
                     const float *wavelet, int nsrc, const double *src_coords, int nrec,
                     const double *rec_coords, int snap_interval, float *rec_out, void *stream,

@@ -16,6 +16,7 @@
 #include <functional>
 #include <map>
 #include <mutex>
+#include <set>
 #include <string>
 #include <thread>
 #include <vector>
@@ -103,6 +104,10 @@ struct wp_ctx {
   long long *d_rows = nullptr;            // device row bases read by the sparse kernels
   std::vector<struct GraphEntry *> graphs;
   uint64_t graph_stamp = 0;
+  // states handed out by wp_forward_save and not yet freed: wp_destroy releases
+  // their device memory and detaches them, so a state freed after its context
+  // touches nothing of it
+  std::set<struct wp_state *> states;
 };
 
 // One instantiated graph of a block of time steps, replayable while every
@@ -1488,6 +1493,11 @@ void wp_destroy(wp_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream && !c->broken) cudaStreamSynchronize(c->stream);
+  for (wp_state *st : c->states) {
+    state_release(st);
+    st->c = nullptr;
+  }
+  c->states.clear();
   for (auto &kv : c->live) cudaFreeAsync(kv.first, c->stream);
   for (auto &kv : c->cache) cudaFreeAsync(kv.second, c->stream);
   if (c->stream && !c->broken) cudaStreamSynchronize(c->stream);
@@ -2085,12 +2095,21 @@ int wp_forward_save(wp_ctx *c, const wp_grid *grid, const float *m, const float 
   *state = nullptr;
   TRY(enter(c, stream));
   DEV_ARGS(c, stream, {{m, "m"}, {eta, "eta"}, {wavelet, "wavelet"}, {rec_out, "rec_out"}});
-  return leave(c, stream,
-               forward_save(c, grid, m, eta, wavelet, nsrc, src, nrec, rec, S, rec_out, false, false, state));
+  const int rc = leave(c, stream,
+                       forward_save(c, grid, m, eta, wavelet, nsrc, src, nrec, rec, S, rec_out, false, false, state));
+  if (rc == WP_OK && *state) {
+    c->states.insert(*state);
+  } else if (*state) {
+    state_release(*state);
+    delete *state;
+    *state = nullptr;
+  }
+  return rc;
 }
 
 int wp_backward(wp_state *st, const float *residual, float *grad_out, void *stream) {
   if (!st) return fail(WP_EINVAL, "state is NULL");
+  if (!st->c) return fail(WP_EINVAL, "the state's context has been destroyed");
   TRY(enter(st->c, stream));
   DEV_ARGS(st->c, stream, {{residual, "residual"}, {grad_out, "grad_out"}});
   return leave(st->c, stream, backward(st, residual, grad_out, false, false));
@@ -2249,7 +2268,10 @@ int wp_trim(wp_ctx *c, size_t keep_bytes) {
 
 void wp_state_free(wp_state *st) {
   if (!st) return;
-  state_release(st);
+  if (st->c) {  // still attached: give its blocks back to the context
+    st->c->states.erase(st);
+    state_release(st);
+  }
   delete st;
 }
 

@@ -73,26 +73,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
-// try_wait with a suspend-time hint: a thread whose phase is not complete may
-// sleep up to hint_ns (it wakes when the phase completes) instead of returning
-// after the system-dependent limit, so waiting warps leave the issue slots to
-// the computing ones.
-__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
-      : "memory");
-  return ok != 0;
-}
-
-#ifndef WP_WAIT_HINT_NS
-#define WP_WAIT_HINT_NS 0  // suspend-time hint of the bounded waits (0: the system's own limit)
-#endif
-
 // Non-blocking probe of phase `parity` of `bar` (try_wait may suspend the thread
 // for a while when the phase is not complete; test_wait returns at once).
 __device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
@@ -117,18 +97,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     *abort_flag = 1;
     return false;
   }
-  auto try_once = [&]() -> bool {
-    if constexpr (WP_WAIT_HINT_NS > 0) {
-      const uint32_t hint = static_cast<uint32_t>(limit_ns < WP_WAIT_HINT_NS ? limit_ns : WP_WAIT_HINT_NS);
-      return mbar_try_wait_hint(bar, parity, hint);
-    } else {
-      return mbar_try_wait(bar, parity);
-    }
-  };
-  if (try_once()) return true;
+  if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
   while (true) {
-    if (try_once()) return true;
+    if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
     if (global_timer_ns() - t0 > limit_ns) {
       *abort_flag = 1;

@@ -160,3 +160,27 @@ def test_device_calls_refuse_host_and_short_buffers():
         W.wp_forward_dev(c.handle, wg, m, eta, qd, model.src, model.rec, out)
         torch.cuda.synchronize()
         assert rel_l2(out.cpu().numpy(), ref) < 1e-4
+
+
+def test_state_outliving_its_context_is_detached():
+    # a forward state kept (e.g. by an autograd graph held in a traceback) after
+    # its context is destroyed: the context releases the state's memory, backward
+    # on it is refused, and freeing it afterwards touches nothing of the context
+    model, og, wg, q = case((20, 22, 24), 4, 12, seed=4)
+    m = torch.from_numpy(model.m32()).cuda()
+    eta = torch.from_numpy(model.eta32()).cuda()
+    qd = torch.from_numpy(q).cuda()
+    d = torch.zeros((wg.nt, len(model.rec)), device="cuda")
+    c = W.Context(0)
+    st = W.wp_forward_save(c.handle, wg, m, eta, qd, model.src, model.rec, 4, d)
+    g = torch.zeros_like(m)
+    W.wp_backward(st, d, g)
+    c.close()
+    with pytest.raises(W.WpError) as e:
+        W.wp_backward(st, d, g)
+    assert e.value.status == W.WP_EINVAL
+    W.wp_state_free(st)
+    # a new context still works
+    with W.Context(0) as c2:
+        ref = O.forward(og, model.m32(), model.eta32(), q, model.src, model.rec)
+        assert rel_l2(run_dev(c2.handle, wg, model, q), ref) < 1e-4
