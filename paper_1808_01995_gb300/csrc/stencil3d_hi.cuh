@@ -46,6 +46,9 @@ namespace wp {
 #ifndef WP_HI_ZU
 #define WP_HI_ZU 4       // planes per unrolled z step
 #endif
+#ifndef WP_HI_ZALT
+#define WP_HI_ZALT 1        // odd z-chunks of a column swept downward
+#endif
 #ifndef WP_HI_SPLIT_REGS
 #define WP_HI_SPLIT_REGS 1  // producer warpgroup gives its registers to the consumer warpgroups (setmaxnreg)
 #endif
@@ -134,12 +137,19 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
 
   const int ncta = static_cast<int>(gridDim.x);
   const int cta = static_cast<int>(blockIdx.x);
-  auto item_geom = [&](int item, int &tx, int &ty, int &z0, int &z1) {
+  // With WP_HI_ZALT, odd chunks of a column are swept downward, so that two
+  // adjacent chunks read the planes around their common face at about the same
+  // time (both at the end of their sweeps) and the second read hits L2.  Loops run
+  // over a sweep index z in [z0, z1) (halos z0 - R .. z1 - 1 + R); phys() maps it
+  // to the plane.  The z neighbours' sums are symmetric, so results do not depend
+  // on the direction.
+  auto item_geom = [&](int item, int &tx, int &ty, int &z0, int &z1, int &dir) {
     const int tile = item / a.nzc, zc = item - tile * a.nzc;
     tx = tile % a.tiles_x;
     ty = tile / a.tiles_x;
     z0 = a.bz0 + zc * a.zchunk;
     z1 = min(z0 + a.zchunk, a.bz1);
+    dir = (WP_HI_ZALT && (zc & 1)) ? -1 : 1;
   };
 
   if (warp >= W) {
@@ -165,9 +175,10 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
         return false;
       };
       for (int item = cta; item < a.nitems && ok; item += ncta) {
-        int tx, ty, z0, z1;
-        item_geom(item, tx, ty, z0, z1);
+        int tx, ty, z0, z1, dir;
+        item_geom(item, tx, ty, z0, z1, dir);
         if (z0 >= z1) continue;
+        auto phys = [&](int p) -> int { return dir > 0 ? p : z0 + z1 - 1 - p; };
         const int x0 = a.bx0 + tx * TX, y0 = a.by0 + ty * TY;
         const int fx0 = x0 / kFlagTX, fx1 = min((x0 + TX - 1) / kFlagTX + 1, a.flag_tiles_x);
         const int fy0 = y0 / kTileFlagTY, fy1 = min((y0 + TY - 1) / kTileFlagTY + 1, a.flag_tiles_y);
@@ -179,9 +190,10 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
                 v |= __ldg(a.tbits + (static_cast<long long>(fy) * a.flag_tiles_x + fx) * a.nzw + w);
           return v;
         };
-        int wcur = z0 >> 5;
+        int wcur = phys(z0) >> 5;
         unsigned bits = word(wcur);
-        for (int z = z0; z < z1 && ok; ++z) {
+        for (int zs = z0; zs < z1 && ok; ++zs) {
+          const int z = phys(zs);  // the plane updated at this step of the sweep
           if ((z >> 5) != wcur) {
             wcur = z >> 5;
             bits = word(wcur);
@@ -202,7 +214,7 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
             tma_load_3d(t + C::S_UM * TT, &tm_um, x0, y0, z, &full_t[slot]);
             tma_load_3d(t + C::S_B * TT, &tm_b, x0, y0, z, &full_t[slot]);
             if (d) tma_load_3d(t + C::S_S * TT, &tm_s, x0, y0, z, &full_t[slot]);
-            tma_load_3d(t + C::S_UC * TT, &tm_uc, x0, y0, z + R, &full_t[slot]);
+            tma_load_3d(t + C::S_UC * TT, &tm_uc, x0, y0, phys(zs + R), &full_t[slot]);
             if (MODE == kModeAdjGrad) {
               tma_load_3d(t + C::S_UJ * TT, &tm_uj, x0, y0, z, &full_t[slot]);
               tma_load_3d(t + C::S_G * TT, &tm_g, x0, y0, z, &full_t[slot]);
@@ -251,9 +263,10 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
   const V nidt2 = make_float2(a.neg_inv_dt2, a.neg_inv_dt2);
 
   for (int item = cta; item < a.nitems; item += ncta) {
-    int tx, ty, z0, z1;
-    item_geom(item, tx, ty, z0, z1);
+    int tx, ty, z0, z1, dir;
+    item_geom(item, tx, ty, z0, z1, dir);
     if (z0 >= z1) continue;
+    auto phys = [&](int p) -> int { return dir > 0 ? p : z0 + z1 - 1 - p; };
     const int gx = a.bx0 + tx * TX + NX * lane;
     const int y0 = a.by0 + ty * TY;
     const bool xin0 = gx < a.bx1;
@@ -273,7 +286,7 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
     V q[NY][2 * R + C::ZU];
 #pragma unroll
     for (int j = 0; j < 2 * R; ++j) {
-      const int p = z0 - R + j;
+      const int p = phys(z0 - R + j);
       const bool pin = p >= 0 && p < a.g.nz;
       const float *src = a.u + static_cast<long long>(pin ? p : 0) * a.g.plane;
 #pragma unroll
@@ -374,7 +387,8 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
       release(&empty_h[hslot]);
 
       const bool d = sflag[tslot] != 0;
-      const long long po = static_cast<long long>(z) * a.g.plane;
+      const int pz = phys(z);
+      const long long po = static_cast<long long>(pz) * a.g.plane;
       const bool live = !*abort_flag;
 #pragma unroll
       for (int r = 0; r < NY; ++r) {
@@ -388,7 +402,7 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
         if (MODE == kModeAdjGrad)
           gn = vfma(vmul(nidt2, vld<V>(T + C::S_UJ * TT + ti)), vfma(sv, dd, bl), vld<V>(T + C::S_G * TT + ti));
         if (yin[r] && live &&
-            WP_IN_BOUNDS(z >= 0 && z < a.g.nz && y0 + ty0 + r < a.g.ny && (!xin0 || gx < a.g.nx) &&
+            WP_IN_BOUNDS(pz >= 0 && pz < a.g.nz && y0 + ty0 + r < a.g.ny && (!xin0 || gx < a.g.nx) &&
                              (!xin1 || gx + 1 < a.g.nx) && gx >= 0,
                          a.err)) {
           float *op = a.out + po + rofs[r] + gx;
