@@ -981,29 +981,25 @@ static int run_loop(Prop &P, Field3 u[2], int nt, const DevPoints &inj, const fl
   wp_ctx *c = P.c;
   int k0 = 0;
   const int B = graph_block(c, nt);
+  auto one_step = [&](int k, long long row, const long long *rb) -> int {
+    Field3 &cur = u[k & 1], &prv = u[(k + 1) & 1];
+    TRY(prop_step(P, cur, prv, prv.p, kModeFwd, nullptr, nullptr));
+    TRY(prop_inject(P, inj, data, row, prv.p, nullptr, nullptr, rb));
+    if (out) TRY(prop_sample(P, smp, prv.p, out, row, rb));
+    return WP_OK;
+  };
   if (B > 0) {
     long long *rb = c->d_rows;
     CU(launch_set_row(c->stream, rb, dir > 0 ? 0 : nt - 1));
     c->launches++;
     auto block = [&]() -> int {
-      for (int j = 0; j < B; ++j) {
-        Field3 &cur = u[j & 1], &prv = u[(j + 1) & 1];
-        TRY(prop_step(P, cur, prv, prv.p, kModeFwd, nullptr, nullptr));
-        TRY(prop_inject(P, inj, data, dir * j, prv.p, nullptr, nullptr, rb));
-        if (out) TRY(prop_sample(P, smp, prv.p, out, dir * j, rb));
-      }
+      for (int j = 0; j < B; ++j) TRY(one_step(j, dir * j, rb));
       return prop_add_row(c, rb, static_cast<long long>(dir) * B);
     };
     TRY(graph_replay(c, block, nt / B));
     k0 = (nt / B) * B;
   }
-  for (int k = k0; k < nt; ++k) {
-    const long long row = dir > 0 ? k : nt - 1 - k;
-    Field3 &cur = u[k & 1], &prv = u[(k + 1) & 1];
-    TRY(prop_step(P, cur, prv, prv.p, kModeFwd, nullptr, nullptr));
-    TRY(prop_inject(P, inj, data, row, prv.p, nullptr, nullptr));
-    if (out) TRY(prop_sample(P, smp, prv.p, out, row));
-  }
+  for (int k = k0; k < nt; ++k) TRY(one_step(k, dir > 0 ? k : nt - 1 - k, nullptr));
   return WP_OK;
 }
 
@@ -1146,6 +1142,7 @@ struct wp_state {
   float *snaps = nullptr;      // [nseg][2][nfield]: (u^{sS-1}, u^{sS}); S = 1: [nt][nfield] = u^1..u^nt
   int S = 0, nseg = 0;
   std::vector<Field3> hist;    // S = 1: level j (1..nt) at hist[j-1], with its own descriptors
+  std::vector<Field3> snapf;   // S > 1: the snapshot levels, [2 s] = u^{sS-1}, [2 s + 1] = u^{sS}
   PointSet psrc, prec;
   DevPoints dsrc, drec;
   float *wavelet = nullptr;    // [nt][nsrc] device copy
@@ -1236,7 +1233,16 @@ static int forward_save(wp_ctx *c, const wp_grid *grid, const float *m, const fl
         TRY(make_field_maps(&st->hist[size_t(j)], G));
       }
     } else if (st->nseg > 0) {
+      // the step that produces a snapshot level writes it there, and the backward
+      // pass reads it in place: no copies
       TRY(keep.alloc(&st->snaps, size_t(st->nseg) * 2 * G.nfield));
+      st->snapf.resize(2 * size_t(st->nseg));
+      for (size_t i = 0; i < st->snapf.size(); ++i) {
+        st->snapf[i].p = st->snaps + i * G.nfield;
+        TRY(make_field_maps(&st->snapf[i], G));
+      }
+      CU(cudaMemsetAsync(st->snapf[0].p, 0, G.field_bytes(), c->stream));  // u^{-1} = u^0 = 0
+      CU(cudaMemsetAsync(st->snapf[1].p, 0, G.field_bytes(), c->stream));
     }
     float *rec_d = nullptr;
     if (rec_out && n_out) {
@@ -1246,23 +1252,26 @@ static int forward_save(wp_ctx *c, const wp_grid *grid, const float *m, const fl
     Prop &P = st->P;
     // level k of the full history: u^{-1}, u^0 in the zeroed work fields
     auto lev = [&](int k) -> Field3 & { return k == -1 ? u[0] : k == 0 ? u[1] : st->hist[size_t(k - 1)]; };
-    for (int n = 0; st->S == 1 && n < G.nt; ++n) {
-      Field3 &nxt = lev(n + 1);
-      TRY(prop_step(P, lev(n), lev(n - 1), nxt.p, kModeFwd, nullptr, nullptr));
+    // S > 1: level k is snapshot slot 2 s if k = sS - 1, 2 s + 1 if k = sS, else
+    // the work field u[k & 1] (a level there is dead when k + 2 overwrites it)
+    const int S = st->S;
+    auto snap_slot = [&](int k) -> int {
+      if ((k + 1) % S == 0 && (k + 1) / S < st->nseg) return 2 * ((k + 1) / S);
+      if (k >= 0 && k % S == 0 && k / S < st->nseg) return 2 * (k / S) + 1;
+      return -1;
+    };
+    auto slev = [&](int k) -> Field3 & {
+      const int i = snap_slot(k);
+      return i >= 0 ? st->snapf[size_t(i)] : u[k & 1];
+    };
+    auto step = [&](Field3 &cur, Field3 &prv, Field3 &nxt, int n) -> int {
+      TRY(prop_step(P, cur, prv, nxt.p, kModeFwd, nullptr, nullptr));
       TRY(prop_inject(P, st->dsrc, st->wavelet, n, nxt.p, nullptr, nullptr));
       if (rec_d) TRY(prop_sample(P, st->drec, nxt.p, rec_d, n));
-    }
-    for (int n = 0; st->S > 1 && n < G.nt; ++n) {
-      Field3 &cur = u[n & 1], &prv = u[(n + 1) & 1];
-      if (n % st->S == 0) {
-        float *dst = st->snaps + size_t(n / st->S) * 2 * G.nfield;
-        CU(cudaMemcpyAsync(dst, prv.p, G.field_bytes(), cudaMemcpyDeviceToDevice, c->stream));
-        CU(cudaMemcpyAsync(dst + G.nfield, cur.p, G.field_bytes(), cudaMemcpyDeviceToDevice, c->stream));
-      }
-      TRY(prop_step(P, cur, prv, prv.p, kModeFwd, nullptr, nullptr));
-      TRY(prop_inject(P, st->dsrc, st->wavelet, n, prv.p, nullptr, nullptr));
-      if (rec_d) TRY(prop_sample(P, st->drec, prv.p, rec_d, n));
-    }
+      return WP_OK;
+    };
+    for (int n = 0; S == 1 && n < G.nt; ++n) TRY(step(lev(n), lev(n - 1), lev(n + 1), n));
+    for (int n = 0; S > 1 && n < G.nt; ++n) TRY(step(slev(n), slev(n - 1), slev(n + 1), n));
     if (host_rec && rec_d) CU(cudaMemcpyAsync(rec_out, rec_d, n_out * 4, cudaMemcpyDeviceToHost, c->stream));
     TRY(ctx_wait(c, "forward with snapshots"));
     keep.release_all_to(st->mem);
@@ -1324,8 +1333,10 @@ static int backward(wp_state *st, const float *residual, float *grad_out, bool h
                          c->stream));
     return ctx_wait(c, "backward (adjoint, gradient from the full history)");
   }
+  // ring[2 ..] receive the recomputed levels; [0], [1] stand for the segment's
+  // snapshot pair, read in place
   std::vector<Field3> ring(size_t(std::min(S, std::max(G.nt, 1))) + 2);
-  for (auto &f : ring) TRY(alloc_field(tmp, G, &f, false, c->stream));
+  for (size_t i = 2; i < ring.size(); ++i) TRY(alloc_field(tmp, G, &ring[i], false, c->stream));
   Field3 w[2], g;
   TRY(alloc_field(tmp, G, &w[0], true, c->stream));
   TRY(alloc_field(tmp, G, &w[1], true, c->stream));
@@ -1334,9 +1345,8 @@ static int backward(wp_state *st, const float *residual, float *grad_out, bool h
   for (int s = st->nseg - 1; s >= 0; --s) {
     const int s0 = s * S;
     const int len = std::min(S, G.nt - s0);
-    const float *snap = st->snaps + size_t(s) * 2 * G.nfield;
-    CU(cudaMemcpyAsync(ring[0].p, snap, G.field_bytes(), cudaMemcpyDeviceToDevice, c->stream));
-    CU(cudaMemcpyAsync(ring[1].p, snap + G.nfield, G.field_bytes(), cudaMemcpyDeviceToDevice, c->stream));
+    ring[0] = st->snapf[2 * size_t(s)];
+    ring[1] = st->snapf[2 * size_t(s) + 1];
     {
       NvtxRange rr("wp.recompute");
       for (int i = 0; i < len; ++i) {  // recompute u^{s0+1} .. u^{s0+len} into ring[2..]

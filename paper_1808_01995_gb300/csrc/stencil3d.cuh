@@ -111,6 +111,8 @@ struct Stencil3dArgs {
   unsigned long long wait_ns;   // a wait gives up after this long (0: unless already complete)
 };
 
+
+
 // ---- scalar / packed-pair arithmetic -------------------------------------
 template <int NX> struct Vec;
 template <> struct Vec<1> { typedef float T; };
@@ -344,7 +346,10 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
     for (int j = 0; j < R; ++j) {
       const uint32_t pos = ub + j;
       const uint32_t slot = pos % C::NSU;
-      mbar_wait_bounded(&full_u[slot], (pos / C::NSU) & 1, abort_flag, a.wait_ns);
+      if (j == 0)  // the item's first wait
+        mbar_wait_first(&full_u[slot], (pos / C::NSU) & 1, abort_flag, a.wait_ns);
+      else
+        mbar_wait_bounded(&full_u[slot], (pos / C::NSU) & 1, abort_flag, a.wait_ns);
       const float *P = uring + slot * (C::USLOT / 4);
 #pragma unroll
       for (int r = 0; r < NY; ++r) q[r][R + j] = vld<V>(P + (ty0 + r + R) * C::PW + cx0);

@@ -297,6 +297,9 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
       }
     }
 
+    // the item's first wait (with a zero limit it does not block)
+    if (a.wait_ns == 0) mbar_wait_first(&full_t[tpos & (C::NT - 1)], (tpos / C::NT) & 1, abort_flag, 0);
+
     auto plane = [&](int z, auto oc) {
       constexpr int o = decltype(oc)::value;
       // pointwise tiles of plane z (and the centre of plane z + R)

@@ -88,16 +88,16 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Wait for phase `parity` of `bar`; false (and *abort set) once limit_ns has
-// passed, or when another thread of the block has already aborted.  With
-// limit_ns = 0 a phase that is not complete at the first look gives up at once.
+// passed, or when another thread of the block has already aborted.  The fast path
+// is a single try_wait; the limit is read only when that fails (limit_ns = 0: give
+// up at once).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
                                                   uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
   if (limit_ns == 0) {
-    if (mbar_test_wait(bar, parity)) return true;
     *abort_flag = 1;
     return false;
   }
-  if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -107,6 +107,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
       return false;
     }
   }
+}
+
+// The first wait of a work item: as mbar_wait_bounded, but with limit_ns = 0 the
+// first look does not block (a try_wait may suspend until the phase completes), so
+// that a zero limit gives up at the first copy still in flight.
+__device__ __forceinline__ bool mbar_wait_first(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                                uint64_t limit_ns) {
+  if (limit_ns == 0 && !mbar_test_wait(bar, parity)) {
+    *abort_flag = 1;
+    return false;
+  }
+  return mbar_wait_bounded(bar, parity, abort_flag, limit_ns);
 }
 
 // 3D tiled TMA load of a box at element coordinates (x, y, z) into shared memory,
