@@ -46,14 +46,14 @@ namespace wp {
 #ifndef WP_HI_ZU
 #define WP_HI_ZU 4       // planes per unrolled z step
 #endif
+#ifndef WP_HI_DEC
+#define WP_HI_DEC 40        // registers per thread left to the producer warpgroup
+#endif
 #ifndef WP_HI_ZALT
 #define WP_HI_ZALT 1        // odd z-chunks of a column swept downward
 #endif
 #ifndef WP_HI_SPLIT_REGS
 #define WP_HI_SPLIT_REGS 1  // producer warpgroup gives its registers to the consumer warpgroups (setmaxnreg)
-#endif
-#ifndef WP_HI_SCALAR
-#define WP_HI_SCALAR 0   // scalar FP32 arithmetic instead of packed pairs (a sweep option)
 #endif
 
 template <int R, int MODE>
@@ -88,7 +88,7 @@ struct CfgHi {
   static constexpr bool SPLIT_REGS = WP_HI_SPLIT_REGS != 0 && W % 4 == 0;
   static constexpr int THREADS = SPLIT_REGS ? (W + 4) * 32 : (W + 1) * 32;
   static constexpr int LAUNCH_REGS = (65536 / ((THREADS + 127) / 128 * 128)) / 8 * 8;
-  static constexpr int DEC = 40;
+  static constexpr int DEC = WP_HI_DEC;
   static constexpr int INC_RAW = (THREADS * LAUNCH_REGS - 128 * DEC) / (W * 32) / 8 * 8;
   static constexpr int INC = INC_RAW > 248 ? 248 : INC_RAW;
   static_assert(!SPLIT_REGS || W * 32 * INC + 128 * DEC <= THREADS * LAUNCH_REGS, "register split over the launch");
@@ -96,6 +96,12 @@ struct CfgHi {
   static_assert(TSLOT % 128 == 0, "tile slots must stay 128-byte aligned");
   static_assert(RX >= RE, "x halo must cover the x window");
 };
+
+// f(integral_constant<int, I>) for I = 0 .. N - 1, unrolled at compile time
+template <class F, int... I>
+__device__ __forceinline__ void hi_unroll(F &&f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
 
 // tm: [0] u^n halo'd plane box, [1] u^{n-1}, [2] b, [3] s, [4] u^j, [5] g, [6] u^n (tile boxes)
 // ISO: the three axes have the same spacing (cx = cy = cz): one coefficient per
@@ -332,30 +338,6 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
           };
           auto ysum = [&](int j) -> V { return vadd(col[R + r + j], col[R + r - j]); };
           auto zsum = [&](int j) -> V { return vadd(q[r][o + R + j], q[r][o + R - j]); };
-#if WP_HI_SCALAR
-          // two scalar chains per partial sum (coefficients as constant operands)
-          float l2[2];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            auto pick = [&](V v) -> float { return h ? v.y : v.x; };
-            auto xs = [&](int j) -> float { return win(C::RE + h + j) + win(C::RE + h - j); };
-            auto ys = [&](int j) -> float { return pick(col[R + r + j]) + pick(col[R + r - j]); };
-            auto zs = [&](int j) -> float { return pick(q[r][o + R + j]) + pick(q[r][o + R - j]); };
-            float lx = a.c.c0 * pick(q[r][o + R]);
-            float ly = a.c.cy[1] * ys(1);
-            float lz = a.c.cz[1] * zs(1);
-#pragma unroll
-            for (int j = 1; j <= R; ++j) {
-              lx = fmaf(a.c.cx[j], xs(j), lx);
-              if (j > 1) {
-                ly = fmaf(a.c.cy[j], ys(j), ly);
-                lz = fmaf(a.c.cz[j], zs(j), lz);
-              }
-            }
-            l2[h] = lx + (ly + lz);
-          }
-          lap[r] = make_float2(l2[0], l2[1]);
-#else
           if constexpr (ISO) {
             // two chains (odd and even distances) of the six-neighbour sums
             auto nsum = [&](int j) -> V { return vadd(vadd(xsum(j), ysum(j)), zsum(j)); };
@@ -384,7 +366,6 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
             }
           }
           lap[r] = vadd(lx, vadd(ly, lz));
-#endif
         }
       }
       release(&empty_h[hslot]);
@@ -430,10 +411,7 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
     };
     int z = z0;
     for (; z + C::ZU <= z1; z += C::ZU) {
-      plane(z, std::integral_constant<int, 0>{});
-      if constexpr (C::ZU > 1) plane(z + 1, std::integral_constant<int, 1>{});
-      if constexpr (C::ZU > 2) plane(z + 2, std::integral_constant<int, 2>{});
-      if constexpr (C::ZU > 3) plane(z + 3, std::integral_constant<int, 3>{});
+      hi_unroll([&](auto oc) { plane(z + decltype(oc)::value, oc); }, std::make_integer_sequence<int, C::ZU>{});
       rotate(std::integral_constant<int, C::ZU>{});
     }
     for (; z < z1; ++z) {
