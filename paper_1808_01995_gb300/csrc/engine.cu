@@ -96,6 +96,16 @@ struct wp_ctx {
   uint64_t prof_count = 0;
   std::vector<cudaEvent_t> *prof_ev = nullptr;  // where the next stencil events go
   size_t *prof_n = nullptr;
+  // Programmatic dependent launch inside the time loop: a step kernel whose
+  // predecessor on the stream is another step kernel (chain) may start launching
+  // while that one still runs (its blocks wait for it on the device), hiding the
+  // launch gaps between the stencil, injection and interpolation of a step.
+  // pdl_mode: 0 never, 1 (default) at every order, 2 only with the stencil kernel
+  // of half-orders up to 4.  Measured on 336^3 shots of 1000 steps: SO16 1.5 us
+  // less per step, SO8 within the noise of 1 us.
+  int pdl_mode = 1;
+  bool pdl_scope = false;  // inside a time loop that uses it
+  bool chain = false;      // the last operation enqueued was a step kernel
   // CUDA graphs of time-loop blocks (see graph_replay)
   bool use_graphs = true;
   bool hashing = false, capturing = false;
@@ -670,7 +680,31 @@ static void hash_bytes(wp_ctx *c, const void *p, size_t n) {
   c->hash = h;
 }
 
+// Whether the next step kernel may use a programmatic launch; every step-kernel
+// launcher calls it once and then marks the chain (in hashing mode too, so that
+// the hashed and the captured block decide alike).
+static bool pdl_next(wp_ctx *c) {
+  const bool p = c->pdl_scope && c->chain;
+  c->chain = true;
+  return p;
+}
+
+// Scope of one time loop of half-order R: programmatic launches only between its
+// step kernels, as pdl_mode allows.
+struct PdlScope {
+  wp_ctx *c;
+  PdlScope(wp_ctx *ctx, int R) : c(ctx) {
+    c->pdl_scope = c->pdl_mode == 1 || (c->pdl_mode == 2 && R <= 4);
+    c->chain = false;
+  }
+  ~PdlScope() {
+    c->pdl_scope = false;
+    c->chain = false;
+  }
+};
+
 static int prof_mark(wp_ctx *c) {
+  c->chain = false;  // an event record sits between the kernels around it
   if (!c->profiling) return WP_OK;
   if (c->hashing) {
     c->hash_marks++;
@@ -764,6 +798,7 @@ static int prop_step(Prop &P, const Field3 &u, const Field3 &um, float *out, int
     a.nitems = pl.nitems;
     a.err = P.c->d_scalars;
     a.wait_ns = P.c->wait_ns;
+    a.pdl = pdl_next(P.c);
     const CUtensorMap maps[7] = {u.halo[mode], um.tile[mode], P.b.tile[mode], P.s.tile[mode],
                                  uj ? uj->tile[mode] : P.b.tile[mode], grad ? grad->tile[mode] : P.b.tile[mode],
                                  u.tile[mode]};
@@ -790,6 +825,7 @@ static int prop_step(Prop &P, const Field3 &u, const Field3 &um, float *out, int
     a.grad = grad ? grad->p : nullptr;
     a.uj = uj ? uj->p : nullptr;
     a.neg_inv_dt2 = P.neg_inv_dt2;
+    a.pdl = pdl_next(P.c);
     if (P.c->hashing) {
       hash_bytes(P.c, &mode, sizeof mode);
       hash_bytes(P.c, &a, sizeof a);
@@ -828,6 +864,7 @@ static int prop_inject(Prop &P, const DevPoints &dp, const float *data, long lon
   a.neg_inv_dt2 = P.neg_inv_dt2;
   a.nfield = P.G.nfield;
   a.err = P.c->d_scalars;
+  a.pdl = pdl_next(P.c);
   if (P.c->hashing) {
     hash_bytes(P.c, &a, sizeof a);
     return WP_OK;
@@ -852,6 +889,7 @@ static int prop_sample(Prop &P, const DevPoints &dp, const float *u, float *out,
   a.row = row;
   a.nfield = P.G.nfield;
   a.err = P.c->d_scalars;
+  a.pdl = pdl_next(P.c);
   if (P.c->hashing) {
     hash_bytes(P.c, &a, sizeof a);
     return WP_OK;
@@ -862,12 +900,14 @@ static int prop_sample(Prop &P, const DevPoints &dp, const float *u, float *out,
 }
 
 static int prop_add_row(wp_ctx *c, long long *p, long long d) {
+  const bool pdl = pdl_next(c);
   if (c->hashing) {
     hash_bytes(c, &p, sizeof p);
     hash_bytes(c, &d, sizeof d);
+    hash_bytes(c, &pdl, sizeof pdl);
     return WP_OK;
   }
-  CU(launch_add_row(c->stream, p, d));
+  CU(launch_add_row(c->stream, p, d, pdl));
   c->launches++;
   return WP_OK;
 }
@@ -886,6 +926,7 @@ static int graph_replay(wp_ctx *c, F &&block, int replays) {
   c->hash_marks = 0;
   const uint64_t seq0 = c->prof_seq;
   c->prof_seq = 0;
+  c->chain = false;  // a graph's first kernel has no kernel before it inside the graph
   int rc = block();
   c->hashing = false;
   TRY(rc);
@@ -912,6 +953,7 @@ static int graph_replay(wp_ctx *c, F &&block, int replays) {
     c->capturing = true;
     cudaGraph_t g = nullptr;
     c->prof_seq = 0;
+    c->chain = false;
     cudaError_t be = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
     int brc = be == cudaSuccess ? block() : WP_OK;
     cudaError_t ee = be == cudaSuccess ? cudaStreamEndCapture(c->stream, &g) : be;
@@ -938,6 +980,7 @@ static int graph_replay(wp_ctx *c, F &&block, int replays) {
   }
   c->prof_seq = seq0;
   e->stamp = ++c->graph_stamp;
+  c->chain = false;  // the work after the replays follows a graph launch
   for (int r = 0; r < replays; ++r) {
     CU(cudaGraphLaunch(e->exec, c->stream));
     c->launches += e->kernels;
@@ -979,6 +1022,7 @@ static int alloc_field(Arena &ar, const Geom &G, Field3 *f, bool zero, cudaStrea
 static int run_loop(Prop &P, Field3 u[2], int nt, const DevPoints &inj, const float *data, const DevPoints &smp,
                     float *out, int dir) {
   wp_ctx *c = P.c;
+  PdlScope pdl_scope(c, P.G.R);
   int k0 = 0;
   const int B = graph_block(c, nt);
   auto one_step = [&](int k, long long row, const long long *rb) -> int {
@@ -990,7 +1034,7 @@ static int run_loop(Prop &P, Field3 u[2], int nt, const DevPoints &inj, const fl
   };
   if (B > 0) {
     long long *rb = c->d_rows;
-    CU(launch_set_row(c->stream, rb, dir > 0 ? 0 : nt - 1));
+    CU(launch_set_row(c->stream, rb, dir > 0 ? 0 : nt - 1, pdl_next(c)));
     c->launches++;
     auto block = [&]() -> int {
       for (int j = 0; j < B; ++j) TRY(one_step(j, dir * j, rb));
@@ -1270,8 +1314,11 @@ static int forward_save(wp_ctx *c, const wp_grid *grid, const float *m, const fl
       if (rec_d) TRY(prop_sample(P, st->drec, nxt.p, rec_d, n));
       return WP_OK;
     };
-    for (int n = 0; S == 1 && n < G.nt; ++n) TRY(step(lev(n), lev(n - 1), lev(n + 1), n));
-    for (int n = 0; S > 1 && n < G.nt; ++n) TRY(step(slev(n), slev(n - 1), slev(n + 1), n));
+    {
+      PdlScope pdl_scope(c, G.R);
+      for (int n = 0; S == 1 && n < G.nt; ++n) TRY(step(lev(n), lev(n - 1), lev(n + 1), n));
+      for (int n = 0; S > 1 && n < G.nt; ++n) TRY(step(slev(n), slev(n - 1), slev(n + 1), n));
+    }
     if (host_rec && rec_d) CU(cudaMemcpyAsync(rec_out, rec_d, n_out * 4, cudaMemcpyDeviceToHost, c->stream));
     TRY(ctx_wait(c, "forward with snapshots"));
     keep.release_all_to(st->mem);
@@ -1342,6 +1389,7 @@ static int backward(wp_state *st, const float *residual, float *grad_out, bool h
   TRY(alloc_field(tmp, G, &w[1], true, c->stream));
   TRY(alloc_field(tmp, G, &g, true, c->stream));
   long long kadj = 0;  // adjoint steps done: w^{j+1} in w[kadj & 1]
+  PdlScope pdl_scope(c, G.R);  // only step kernels are enqueued until the copy-out below
   for (int s = st->nseg - 1; s >= 0; --s) {
     const int s0 = s * S;
     const int len = std::min(S, G.nt - s0);
@@ -1363,6 +1411,7 @@ static int backward(wp_state *st, const float *residual, float *grad_out, bool h
     }
   }
   // pitched -> contiguous
+  c->chain = false;
   CU(cudaMemcpy2DAsync(grad_out, size_t(G.nx) * 4, g.p, size_t(G.pitch) * 4, size_t(G.nx) * 4,
                        size_t(G.ny) * G.nz, host_grad ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
   return ctx_wait(c, "backward (recompute, adjoint, gradient)");
@@ -1482,6 +1531,8 @@ int wp_create(wp_ctx **out, int device, size_t budget) {
     c->prof_n = &c->prof_used;
     const char *ng = getenv("WP_NO_GRAPHS");
     c->use_graphs = !(ng && atoi(ng) != 0);
+    const char *np = getenv("WP_PDL");
+    if (np) c->pdl_mode = atoi(np) == 0 ? 0 : atoi(np) == 1 ? 1 : 2;
     CU(cudaMallocHost(&c->h_scalars, 64));
     CU(cudaMemset(c->d_scalars, 0, 64));
     TRY(get_encode());

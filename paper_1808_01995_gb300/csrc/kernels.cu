@@ -17,6 +17,8 @@ template <int R, int MODE>
 __global__ void __launch_bounds__(256) stencil2d_kernel(const Stencil2dArgs a) {
   constexpr int TW = 32, TH = 16, SW = TW + 2 * R, SH = TH + 2 * R;
   __shared__ float tile[SH][SW];
+  grid_dependents_launch();
+  grid_dependency_wait();
   const int x0 = blockIdx.x * TW, z0 = blockIdx.y * TH;
   const int tid = threadIdx.y * 32 + threadIdx.x;
   const int nx = a.g.nx, nz = a.g.nz, pitch = a.g.pitch;
@@ -56,8 +58,7 @@ __global__ void __launch_bounds__(256) stencil2d_kernel(const Stencil2dArgs a) {
 template <int R, int MODE>
 static cudaError_t launch2d_t(cudaStream_t st, const Stencil2dArgs &a) {
   dim3 grid((a.g.nx + 31) / 32, (a.g.nz + 15) / 16);
-  stencil2d_kernel<R, MODE><<<grid, dim3(32, 8), 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_kernel(stencil2d_kernel<R, MODE>, grid, dim3(32, 8), 0, st, a.pdl != 0, a);
 }
 
 template <int MODE>
@@ -338,6 +339,8 @@ cudaError_t launch_zero_outside(cudaStream_t st, float *field, FieldGeom g, Box 
 // grad[t] -= dt^-2 u^j[t] * b[t] * sum_k w_k q_k.
 // ---------------------------------------------------------------------------
 __global__ void inject_kernel(const InjectArgs a) {
+  grid_dependents_launch();
+  grid_dependency_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.ntarget) return;
   const long long row = a.row + (a.row_base ? *a.row_base : 0);
@@ -355,12 +358,13 @@ __global__ void inject_kernel(const InjectArgs a) {
 
 cudaError_t launch_inject(cudaStream_t st, const InjectArgs &a) {
   if (a.ntarget <= 0) return cudaSuccess;
-  inject_kernel<<<(a.ntarget + 127) / 128, 128, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_kernel(inject_kernel, dim3((a.ntarget + 127) / 128), dim3(128), 0, st, a.pdl != 0, a);
 }
 
 // K3: out[row][i] = sum_c w[i][c] u[idx[i][c]].
 __global__ void interp_kernel(const InterpArgs a) {
+  grid_dependents_launch();
+  grid_dependency_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.npts) return;
   float acc = 0.f;
@@ -405,8 +409,7 @@ cudaError_t launch_check_padding(cudaStream_t st, const float *f, FieldGeom g, i
 
 cudaError_t launch_interp(cudaStream_t st, const InterpArgs &a) {
   if (a.npts <= 0) return cudaSuccess;
-  interp_kernel<<<(a.npts + 127) / 128, 128, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_kernel(interp_kernel, dim3((a.npts + 127) / 128), dim3(128), 0, st, a.pdl != 0, a);
 }
 
 // Residual of the misfit J = 1/2 ||d - d_obs||^2 (Eq. AS): r = d - d_obs, and one
@@ -472,17 +475,23 @@ cudaError_t launch_update_model(cudaStream_t st, long long n, float step, const 
   return cudaGetLastError();
 }
 
-__global__ void set_row_kernel(long long *p, long long v) { *p = v; }
-__global__ void add_row_kernel(long long *p, long long d) { *p += d; }
-
-cudaError_t launch_set_row(cudaStream_t st, long long *p, long long v) {
-  set_row_kernel<<<1, 1, 0, st>>>(p, v);
-  return cudaGetLastError();
+__global__ void set_row_kernel(long long *p, long long v) {
+  grid_dependents_launch();
+  grid_dependency_wait();
+  *p = v;
+}
+__global__ void add_row_kernel(long long *p, long long d) {
+  grid_dependents_launch();
+  grid_dependency_wait();
+  *p += d;
 }
 
-cudaError_t launch_add_row(cudaStream_t st, long long *p, long long d) {
-  add_row_kernel<<<1, 1, 0, st>>>(p, d);
-  return cudaGetLastError();
+cudaError_t launch_set_row(cudaStream_t st, long long *p, long long v, bool pdl) {
+  return launch_kernel(set_row_kernel, dim3(1), dim3(1), 0, st, pdl, p, v);
+}
+
+cudaError_t launch_add_row(cudaStream_t st, long long *p, long long d, bool pdl) {
+  return launch_kernel(add_row_kernel, dim3(1), dim3(1), 0, st, pdl, p, d);
 }
 
 }  // namespace wp

@@ -10,6 +10,25 @@ namespace wp {
 
 struct Stencil3dArgs;
 
+// Launch k<<<grid, block, smem, st>>>(args...), with programmatic stream
+// serialization when pdl is set (the kernel must call grid_dependency_wait()
+// before touching memory the previous kernel on the stream reads or writes).
+template <class... KArgs, class... Args>
+inline cudaError_t launch_kernel(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
+                                 Args &&...args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<Args &&>(args)...);
+}
+
 // ---- K1, 3D (stencil3d_fwd.cu / stencil3d_adj.cu; half-orders above 4: stencil3d_hi.cu) ----
 // maps: u^n (halo'd plane box of the mode), u^{n-1}, b, s, u^j, g, u^n (tile boxes of the mode)
 cudaError_t launch_stencil3d_fwd(int R, dim3 grid, cudaStream_t st, const CUtensorMap *maps,
@@ -49,6 +68,7 @@ struct Stencil2dArgs {
   float *grad;        // adjoint+gradient mode
   const float *uj;    // adjoint+gradient mode: forward field u^j
   float neg_inv_dt2;
+  int pdl;            // launch with programmatic stream serialization
 };
 cudaError_t launch_stencil2d(int R, int mode, cudaStream_t st, const Stencil2dArgs &a);
 
@@ -88,6 +108,7 @@ struct InjectArgs {
   float neg_inv_dt2;
   long long nfield;          // elements of a pitched field (debug bounds checks)
   int *err;                  // error word (debug bounds checks)
+  int pdl;                   // launch with programmatic stream serialization
 };
 cudaError_t launch_inject(cudaStream_t st, const InjectArgs &a);
 
@@ -103,6 +124,7 @@ struct InterpArgs {
   long long row;
   long long nfield;          // elements of a pitched field (debug bounds checks)
   int *err;                  // error word (debug bounds checks)
+  int pdl;                   // launch with programmatic stream serialization
 };
 cudaError_t launch_interp(cudaStream_t st, const InterpArgs &a);
 
@@ -111,8 +133,8 @@ cudaError_t launch_interp(cudaStream_t st, const InterpArgs &a);
 cudaError_t launch_check_padding(cudaStream_t st, const float *f, FieldGeom g, int *err);
 
 // *p = v / *p += d (row bases of graph replays), one thread
-cudaError_t launch_set_row(cudaStream_t st, long long *p, long long v);
-cudaError_t launch_add_row(cudaStream_t st, long long *p, long long d);
+cudaError_t launch_set_row(cudaStream_t st, long long *p, long long v, bool pdl);
+cudaError_t launch_add_row(cudaStream_t st, long long *p, long long d, bool pdl);
 
 // ---- misc ----
 // r = d - d_obs over n samples; partial[b] = sum over block b's samples of r^2

@@ -109,6 +109,7 @@ struct Stencil3dArgs {
   // multiple of 4); neighbours outside it are read, only points inside are written
   int bx0, by0, bz0, bx1, by1, bz1;
   unsigned long long wait_ns;   // a wait gives up after this long (0: unless already complete)
+  int pdl;                      // launch with programmatic stream serialization
 };
 
 
@@ -172,6 +173,13 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
     mbar_init_fence();
   }
   __syncthreads();
+  // Under a programmatic launch the kernel before this one on the stream may still
+  // be running: it writes fields read here (and reads the one written here).  The
+  // stencil itself does not let the next kernel launch early: measured, that
+  // kernel's blocks then take SM room in the stencil's last round (SO16 shots
+  // 2 us per step slower; without the early launch 1.5 us faster than no
+  // programmatic launch at all).
+  grid_dependency_wait();
 
   // Items of this CTA, round-robin: in every round the CTAs hold consecutive items
   // (neighbouring tiles and a tile's adjacent z-chunks), so halos meet in L2.

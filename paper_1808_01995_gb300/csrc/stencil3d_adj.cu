@@ -6,8 +6,8 @@ namespace wp {
 
 template <int R>
 static cudaError_t launch_t(dim3 grid, cudaStream_t st, const CUtensorMap *m, const Stencil3dArgs &a) {
-  stencil3d_kernel<R, kModeAdjGrad><<<grid, kThreads3d, Cfg3d<R, kModeAdjGrad>::SMEM, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], a);
-  return cudaGetLastError();
+  return launch_kernel(stencil3d_kernel<R, kModeAdjGrad>, grid, dim3(kThreads3d), Cfg3d<R, kModeAdjGrad>::SMEM, st, a.pdl != 0, m[0],
+                       m[1], m[2], m[3], m[4], m[5], a);
 }
 
 template <int R>

@@ -20,10 +20,10 @@ template <int R, int MODE>
 static cudaError_t launch_t(dim3 grid, cudaStream_t st, const CUtensorMap *m, const Stencil3dArgs &a) {
   using C = CfgHi<R, MODE>;
   if (isotropic(a.c))
-    stencil3d_hi_kernel<R, MODE, true><<<grid, C::THREADS, C::SMEM, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], a);
-  else
-    stencil3d_hi_kernel<R, MODE, false><<<grid, C::THREADS, C::SMEM, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], a);
-  return cudaGetLastError();
+    return launch_kernel(stencil3d_hi_kernel<R, MODE, true>, grid, dim3(C::THREADS), C::SMEM, st, a.pdl != 0, m[0],
+                         m[1], m[2], m[3], m[4], m[5], m[6], a);
+  return launch_kernel(stencil3d_hi_kernel<R, MODE, false>, grid, dim3(C::THREADS), C::SMEM, st, a.pdl != 0, m[0],
+                       m[1], m[2], m[3], m[4], m[5], m[6], a);
 }
 
 template <int R, int MODE, bool ISO>
