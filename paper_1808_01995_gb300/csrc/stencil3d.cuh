@@ -319,6 +319,9 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
     int tx, ty, z0, z1, dir;
     item_geom(item, tx, ty, z0, z1, dir);
     if (z0 >= z1) continue;
+    // with a zero wait limit, look at the item's first copy before anything else
+    // (it is normally still in flight then) and give up if it has not landed
+    if (a.wait_ns == 0) mbar_wait_first(&full_u[ub % C::NSU], (ub / C::NSU) & 1, abort_flag, 0);
     auto phys = [&](int p) -> int { return dir > 0 ? p : z0 + z1 - 1 - p; };
     const int gx = a.bx0 + tx * TX + NX * lane;
     const int y0 = a.by0 + ty * TY;

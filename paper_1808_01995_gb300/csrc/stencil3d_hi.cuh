@@ -28,6 +28,9 @@ namespace wp {
 #ifndef WP_HI_W
 #define WP_HI_W 12       // consumer warps
 #endif
+#ifndef WP_HI_NX
+#define WP_HI_NX 2       // x points per lane (2 or 4)
+#endif
 #ifndef WP_HI_NY
 #define WP_HI_NY 2       // rows per lane, forward
 #endif
@@ -59,13 +62,18 @@ namespace wp {
 template <int R, int MODE>
 struct CfgHi {
   static constexpr int W = WP_HI_W;
-  static constexpr int NX = 2;
+  static constexpr int NX = WP_HI_NX;
+  static constexpr int NP = NX / 2;  // packed pairs of a lane in a row
   static constexpr int NY = MODE == kModeAdjGrad ? WP_HI_NY_ADJ : WP_HI_NY;
   static constexpr int TX = 32 * NX;
   static constexpr int TY = W * NY;
   static constexpr int TT = TX * TY;
   static constexpr int RX = (R + 3) / 4 * 4;  // x halo rounded to 16 bytes
   static constexpr int RE = (R + 1) / 2 * 2;  // x window half-width (even)
+  // a lane's x window: WL columns from WB before its first point (16-byte aligned
+  // loads when NX = 4, 8-byte ones when NX = 2)
+  static constexpr int WB = NX == 4 ? RX : RE;
+  static constexpr int WL = NX == 4 ? NX + 2 * RX : NX + 2 * RE;
   static constexpr int PW = TX + 2 * RX;
   static constexpr int PH = TY + 2 * R;
   static constexpr int NH = WP_HI_NH;
@@ -95,6 +103,8 @@ struct CfgHi {
   static_assert((NH & (NH - 1)) == 0 && (NT & (NT - 1)) == 0, "ring depths must be powers of two");
   static_assert(TSLOT % 128 == 0, "tile slots must stay 128-byte aligned");
   static_assert(RX >= RE, "x halo must cover the x window");
+  static_assert(NX == 2 || NX == 4, "lanes own two or four x points");
+  static_assert(WL % NX == 0 && WB >= R, "x window");
 };
 
 // f(integral_constant<int, I>) for I = 0 .. N - 1, unrolled at compile time
@@ -266,6 +276,7 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
 
   // ---------------- consumers ----------------
   if constexpr (C::SPLIT_REGS) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(C::INC) : "memory");
+  constexpr int NP = C::NP;           // packed pairs of a lane in a row
   const int ty0 = warp * NY;          // first tile row of this lane
   const int cx0 = C::RX + NX * lane;  // this lane's first column in a halo'd plane row
   uint32_t hpos = 0, tpos = 0;        // ring positions of the next plane
@@ -274,44 +285,63 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
     if (lane == 0) mbar_arrive(bar);
   };
   const V nidt2 = make_float2(a.neg_inv_dt2, a.neg_inv_dt2);
+  // the lane's NX consecutive values at p (one 16-byte load when NX = 4) as NP pairs
+  auto ldp = [](const float *p, V *out) {
+    if constexpr (NX == 4) {
+      const float4 v = *reinterpret_cast<const float4 *>(p);
+      out[0] = make_float2(v.x, v.y);
+      out[1] = make_float2(v.z, v.w);
+    } else {
+      out[0] = vld<V>(p);
+    }
+  };
+  auto stp = [](float *p, const V *v) {
+    if constexpr (NX == 4)
+      *reinterpret_cast<float4 *>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    else
+      *reinterpret_cast<V *>(p) = v[0];
+  };
 
   for (int item = cta; item < a.nitems; item += ncta) {
     int tx, ty, z0, z1, dir;
     item_geom(item, tx, ty, z0, z1, dir);
     if (z0 >= z1) continue;
+    // with a zero wait limit, look at the item's first copy before anything else
+    // (it is normally still in flight then) and give up if it has not landed
+    if (a.wait_ns == 0) mbar_wait_first(&full_t[tpos & (C::NT - 1)], (tpos / C::NT) & 1, abort_flag, 0);
     auto phys = [&](int p) -> int { return dir > 0 ? p : z0 + z1 - 1 - p; };
     const int gx = a.bx0 + tx * TX + NX * lane;
     const int y0 = a.by0 + ty * TY;
-    const bool xin0 = gx < a.bx1;
-    const bool xin1 = gx + 1 < a.bx1;
+    int nin = 0;  // this lane's points inside the box: a prefix of its NX points
+#pragma unroll
+    for (int i = 0; i < NX; ++i) nin += gx + i < a.bx1 ? 1 : 0;
     bool yin[NY];
-    int rofs[NY];  // in-plane offset of this lane's point 0 in each row (row clamped inside the grid)
+    int rofs[NY];  // in-plane offset of each row (row clamped inside the grid)
 #pragma unroll
     for (int r = 0; r < NY; ++r) {
       const int gy = y0 + ty0 + r;
       yin[r] = gy < a.by1;
       rofs[r] = min(gy, a.g.ny - 1) * a.g.pitch;
     }
-    const int gxc0 = min(gx, a.g.nx - 1), gxc1 = min(gx + 1, a.g.nx - 1);
 
-    // z queue: q[r][o + j] = u^n at plane z - R + j (o = offset of the plane in an unrolled step);
-    // planes z0 - R .. z0 + R - 1 first, with plain loads
-    V q[NY][2 * R + C::ZU];
+    // z queue: q[r][p][o + j] = u^n at plane z - R + j (o = offset of the plane in an
+    // unrolled step); planes z0 - R .. z0 + R - 1 first, with plain loads
+    V q[NY][NP][2 * R + C::ZU];
 #pragma unroll
     for (int j = 0; j < 2 * R; ++j) {
-      const int p = phys(z0 - R + j);
-      const bool pin = p >= 0 && p < a.g.nz;
-      const float *src = a.u + static_cast<long long>(pin ? p : 0) * a.g.plane;
+      const int pl = phys(z0 - R + j);
+      const bool pin = pl >= 0 && pl < a.g.nz;
+      const float *src = a.u + static_cast<long long>(pin ? pl : 0) * a.g.plane;
 #pragma unroll
       for (int r = 0; r < NY; ++r) {
         const bool ok = pin && yin[r];
-        q[r][j] = make_float2(ok && xin0 ? __ldg(src + rofs[r] + gxc0) : 0.f,
-                              ok && xin1 ? __ldg(src + rofs[r] + gxc1) : 0.f);
+        float v[NX];
+#pragma unroll
+        for (int i = 0; i < NX; ++i) v[i] = ok && i < nin ? __ldg(src + rofs[r] + min(gx + i, a.g.nx - 1)) : 0.f;
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp) q[r][pp][j] = make_float2(v[2 * pp], v[2 * pp + 1]);
       }
     }
-
-    // the item's first wait (with a zero limit it does not block)
-    if (a.wait_ns == 0) mbar_wait_first(&full_t[tpos & (C::NT - 1)], (tpos / C::NT) & 1, abort_flag, 0);
 
     auto plane = [&](int z, auto oc) {
       constexpr int o = decltype(oc)::value;
@@ -321,58 +351,68 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
       ++tpos;
       const float *T = tring + tslot * (C::NSTREAM * TT);
 #pragma unroll
-      for (int r = 0; r < NY; ++r) q[r][2 * R + o] = vld<V>(T + C::S_UC * TT + (ty0 + r) * TX + NX * lane);
+      for (int r = 0; r < NY; ++r) {
+        V t[NP];
+        ldp(T + C::S_UC * TT + (ty0 + r) * TX + NX * lane, t);
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp) q[r][pp][2 * R + o] = t[pp];
+      }
       // x / y neighbours from the halo'd plane z
       const uint32_t hslot = hpos & (C::NH - 1);
       mbar_wait_bounded(&full_h[hslot], (hpos / C::NH) & 1, abort_flag, a.wait_ns);
       ++hpos;
       const float *P = hring + hslot * (C::HSLOT / 4);
-      V lap[NY];
+      V lap[NY][NP];
       {
-        V col[NY + 2 * R];
+        V col[NY + 2 * R][NP];
 #pragma unroll
-        for (int i = 0; i < NY + 2 * R; ++i) col[i] = vld<V>(P + (ty0 + i) * C::PW + cx0);
+        for (int i = 0; i < NY + 2 * R; ++i) ldp(P + (ty0 + i) * C::PW + cx0, col[i]);
 #pragma unroll
         for (int r = 0; r < NY; ++r) {
-          const float *pc = P + (ty0 + r + R) * C::PW + cx0;
-          float2 w[C::RE + 1];
+          // window w = columns cx0 - WB .. cx0 - WB + WL - 1 of the row, as pairs
+          const float *pc = P + (ty0 + r + R) * C::PW + cx0 - C::WB;
+          V w[C::WL / 2];
 #pragma unroll
-          for (int k = 0; k <= C::RE; ++k) w[k] = vld<float2>(pc - C::RE + 2 * k);
+          for (int k = 0; k < C::WL / NX; ++k) ldp(pc + NX * k, &w[NP * k]);
           auto win = [&](int i) -> float { return (i & 1) ? w[i >> 1].y : w[i >> 1].x; };
-          auto xsum = [&](int j) -> float2 {
-            if ((j & 1) == 0) return __fadd2_rn(w[(C::RE + j) >> 1], w[(C::RE - j) >> 1]);
-            return make_float2(win(C::RE + j) + win(C::RE - j), win(C::RE + 1 + j) + win(C::RE + 1 - j));
-          };
-          auto ysum = [&](int j) -> V { return vadd(col[R + r + j], col[R + r - j]); };
-          auto zsum = [&](int j) -> V { return vadd(q[r][o + R + j], q[r][o + R - j]); };
-          if constexpr (ISO) {
-            // two chains (odd and even distances) of the six-neighbour sums
-            auto nsum = [&](int j) -> V { return vadd(vadd(xsum(j), ysum(j)), zsum(j)); };
-            V la = vfma(a.c.px[1], nsum(1), vmul(a.c.p0, q[r][o + R]));
-            V lb = vmul(a.c.px[2], nsum(2));
 #pragma unroll
-            for (int j = 3; j <= R; ++j) {
-              if (j & 1)
-                la = vfma(a.c.px[j], nsum(j), la);
-              else
-                lb = vfma(a.c.px[j], nsum(j), lb);
-            }
-            lap[r] = vadd(la, lb);
-            continue;
-          }
-          // three partial sums (x, y, z) keep every chain of dependent FMAs at most R long
-          V lx = vmul(a.c.p0, q[r][o + R]);
-          V ly = vmul(a.c.py[1], ysum(1));
-          V lz = vmul(a.c.pz[1], zsum(1));
+          for (int pp = 0; pp < NP; ++pp) {
+            const int c0 = C::WB + 2 * pp;  // window index of the pair's first point
+            auto xsum = [&](int j) -> V {
+              if ((j & 1) == 0) return vadd(w[(c0 + j) >> 1], w[(c0 - j) >> 1]);
+              return make_float2(win(c0 + j) + win(c0 - j), win(c0 + 1 + j) + win(c0 + 1 - j));
+            };
+            auto ysum = [&](int j) -> V { return vadd(col[R + r + j][pp], col[R + r - j][pp]); };
+            auto zsum = [&](int j) -> V { return vadd(q[r][pp][o + R + j], q[r][pp][o + R - j]); };
+            if constexpr (ISO) {
+              // two chains (odd and even distances) of the six-neighbour sums
+              auto nsum = [&](int j) -> V { return vadd(vadd(xsum(j), ysum(j)), zsum(j)); };
+              V la = vfma(a.c.px[1], nsum(1), vmul(a.c.p0, q[r][pp][o + R]));
+              V lb = vmul(a.c.px[2], nsum(2));
 #pragma unroll
-          for (int j = 1; j <= R; ++j) {
-            lx = vfma(a.c.px[j], xsum(j), lx);
-            if (j > 1) {
-              ly = vfma(a.c.py[j], ysum(j), ly);
-              lz = vfma(a.c.pz[j], zsum(j), lz);
+              for (int j = 3; j <= R; ++j) {
+                if (j & 1)
+                  la = vfma(a.c.px[j], nsum(j), la);
+                else
+                  lb = vfma(a.c.px[j], nsum(j), lb);
+              }
+              lap[r][pp] = vadd(la, lb);
+            } else {
+              // three partial sums (x, y, z) keep every chain of dependent FMAs at most R long
+              V lx = vmul(a.c.p0, q[r][pp][o + R]);
+              V ly = vmul(a.c.py[1], ysum(1));
+              V lz = vmul(a.c.pz[1], zsum(1));
+#pragma unroll
+              for (int j = 1; j <= R; ++j) {
+                lx = vfma(a.c.px[j], xsum(j), lx);
+                if (j > 1) {
+                  ly = vfma(a.c.py[j], ysum(j), ly);
+                  lz = vfma(a.c.pz[j], zsum(j), lz);
+                }
+              }
+              lap[r][pp] = vadd(lx, vadd(ly, lz));
             }
           }
-          lap[r] = vadd(lx, vadd(ly, lz));
         }
       }
       release(&empty_h[hslot]);
@@ -384,26 +424,43 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
 #pragma unroll
       for (int r = 0; r < NY; ++r) {
         const int ti = (ty0 + r) * TX + NX * lane;
-        const V c = q[r][o + R];
-        const V dd = vsub(c, vld<V>(T + C::S_UM * TT + ti));
-        const V sv = d ? vld<V>(T + C::S_S * TT + ti) : make_float2(0.f, 0.f);
-        const V bl = vmul(vld<V>(T + C::S_B * TT + ti), lap[r]);
-        const V un = vadd(vfma(sv, dd, vadd(c, dd)), bl);
-        V gn = make_float2(0.f, 0.f);
-        if (MODE == kModeAdjGrad)
-          gn = vfma(vmul(nidt2, vld<V>(T + C::S_UJ * TT + ti)), vfma(sv, dd, bl), vld<V>(T + C::S_G * TT + ti));
-        if (yin[r] && live &&
-            WP_IN_BOUNDS(pz >= 0 && pz < a.g.nz && y0 + ty0 + r < a.g.ny && (!xin0 || gx < a.g.nx) &&
-                             (!xin1 || gx + 1 < a.g.nx) && gx >= 0,
+        V um[NP], bv[NP], sv[NP], uj[NP], gv[NP], un[NP], gn[NP];
+        ldp(T + C::S_UM * TT + ti, um);
+        ldp(T + C::S_B * TT + ti, bv);
+        if (d) {
+          ldp(T + C::S_S * TT + ti, sv);
+        } else {
+#pragma unroll
+          for (int pp = 0; pp < NP; ++pp) sv[pp] = make_float2(0.f, 0.f);
+        }
+        if (MODE == kModeAdjGrad) {
+          ldp(T + C::S_UJ * TT + ti, uj);
+          ldp(T + C::S_G * TT + ti, gv);
+        }
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp) {
+          const V c = q[r][pp][o + R];
+          const V dd = vsub(c, um[pp]);
+          const V bl = vmul(bv[pp], lap[r][pp]);
+          un[pp] = vadd(vfma(sv[pp], dd, vadd(c, dd)), bl);
+          if (MODE == kModeAdjGrad) gn[pp] = vfma(vmul(nidt2, uj[pp]), vfma(sv[pp], dd, bl), gv[pp]);
+        }
+        if (yin[r] && nin > 0 && live &&
+            WP_IN_BOUNDS(pz >= 0 && pz < a.g.nz && y0 + ty0 + r < a.g.ny && gx >= 0 && gx + nin - 1 < a.g.nx,
                          a.err)) {
           float *op = a.out + po + rofs[r] + gx;
           float *gp = a.grad + po + rofs[r] + gx;
-          if (xin1) {
-            *reinterpret_cast<float2 *>(op) = un;
-            if (MODE == kModeAdjGrad) *reinterpret_cast<float2 *>(gp) = gn;
-          } else if (xin0) {
-            op[0] = un.x;
-            if (MODE == kModeAdjGrad) gp[0] = gn.x;
+          if (nin == NX) {
+            stp(op, un);
+            if (MODE == kModeAdjGrad) stp(gp, gn);
+          } else {
+#pragma unroll
+            for (int i = 0; i < NX - 1; ++i) {
+              if (i < nin) {
+                op[i] = (i & 1) ? un[i >> 1].y : un[i >> 1].x;
+                if (MODE == kModeAdjGrad) gp[i] = (i & 1) ? gn[i >> 1].y : gn[i >> 1].x;
+              }
+            }
           }
         }
       }
@@ -414,7 +471,9 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
 #pragma unroll
       for (int r = 0; r < NY; ++r)
 #pragma unroll
-        for (int j = 0; j < 2 * R; ++j) q[r][j] = q[r][j + n];
+        for (int pp = 0; pp < NP; ++pp)
+#pragma unroll
+          for (int j = 0; j < 2 * R; ++j) q[r][pp][j] = q[r][pp][j + n];
     };
     int z = z0;
     for (; z + C::ZU <= z1; z += C::ZU) {
