@@ -265,8 +265,9 @@ void wp_state_free(wp_state *state);
  * kernel waits for its own TMA copies and ring slots; default 2 s, at most 60).
  * A wait that runs out makes the kernel skip its remaining stores and the call
  * return WP_EDEVICE; the context stays usable (set a larger limit and call
- * again).  0 means that any wait which is not already complete at its first look
- * gives up at once: it exists to exercise that error path. */
+ * again).  0 makes every stencil kernel give up at the start of its first work
+ * item (a wait on a barrier that nothing completes), and any later wait that is
+ * not complete at once: it exists to exercise that error path deterministically. */
 int wp_set_wait_limit(wp_ctx *ctx, double seconds);
 
 /* ---- The computational-fluid-dynamics examples of Sec. 5 (2D, FP32) --------

@@ -87,7 +87,7 @@ struct Cfg3d {
   static constexpr int TSLOT = TX * TY * 4;                          // bytes per tile
   static constexpr int T_OFF = NSU * USLOT;
   static constexpr int BAR_OFF = T_OFF + NST * NSTREAM * TSLOT;
-  static constexpr int SMEM = BAR_OFF + 2 * (NSU + NST) * 8 + NST * 4 + 16;
+  static constexpr int SMEM = BAR_OFF + (2 * (NSU + NST) + 1) * 8 + NST * 4 + 16;
   static_assert(RX >= RE, "x halo must cover the x window");
 };
 
@@ -108,7 +108,7 @@ struct Stencil3dArgs {
   // updated box [bx0, bx1) x [by0, by1) x [bz0, bz1) (the whole grid normally; bx0 a
   // multiple of 4); neighbours outside it are read, only points inside are written
   int bx0, by0, bz0, bx1, by1, bz1;
-  unsigned long long wait_ns;   // a wait gives up after this long (0: unless already complete)
+  unsigned long long wait_ns;   // a wait gives up after this long (0: at each item's start, see wp_set_wait_limit)
   int pdl;                      // launch with programmatic stream serialization
 };
 
@@ -150,7 +150,8 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
   uint64_t *empty_u = full_u + C::NSU;
   uint64_t *full_t = empty_u + C::NSU;
   uint64_t *empty_t = full_t + C::NST;
-  volatile int *sflag = reinterpret_cast<volatile int *>(empty_t + C::NST);  // [NST]: s loaded
+  uint64_t *never = empty_t + C::NST;  // completed by nothing: the zero wait limit's first wait
+  volatile int *sflag = reinterpret_cast<volatile int *>(never + 1);  // [NST]: s loaded
   volatile int *abort_flag = sflag + C::NST;
 
   const int tid = threadIdx.x;
@@ -169,6 +170,7 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
       mbar_init(&full_t[i], 1);
       mbar_init(&empty_t[i], kConsumerWarps);
     }
+    mbar_init(never, 1);
     *abort_flag = 0;
     mbar_init_fence();
   }
@@ -319,9 +321,8 @@ __global__ void __launch_bounds__(kThreads3d, Cfg3d<R, MODE>::MINB)
     int tx, ty, z0, z1, dir;
     item_geom(item, tx, ty, z0, z1, dir);
     if (z0 >= z1) continue;
-    // with a zero wait limit, look at the item's first copy before anything else
-    // (it is normally still in flight then) and give up if it has not landed
-    if (a.wait_ns == 0) mbar_wait_first(&full_u[ub % C::NSU], (ub / C::NSU) & 1, abort_flag, 0);
+    // a zero wait limit gives up here, on a barrier that nothing completes
+    if (a.wait_ns == 0) mbar_wait_first(never, 0, abort_flag, 0);
     auto phys = [&](int p) -> int { return dir > 0 ? p : z0 + z1 - 1 - p; };
     const int gx = a.bx0 + tx * TX + NX * lane;
     const int y0 = a.by0 + ty * TY;

@@ -86,7 +86,7 @@ struct CfgHi {
   static constexpr int TSLOT = TT * 4;
   static constexpr int T_OFF = NH * HSLOT;
   static constexpr int BAR_OFF = T_OFF + NT * NSTREAM * TSLOT;
-  static constexpr int SMEM = BAR_OFF + 2 * (NH + NT) * 8 + NT * 4 + 16;
+  static constexpr int SMEM = BAR_OFF + (2 * (NH + NT) + 1) * 8 + NT * 4 + 16;
   // Without the register split: W consumer warps and one producer warp.  With it
   // (W a multiple of 4): W/4 consumer warpgroups and one producer warpgroup whose
   // first lane issues the copies; the producer warpgroup drops to DEC registers per
@@ -132,7 +132,8 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
   uint64_t *empty_h = full_h + C::NH;
   uint64_t *full_t = empty_h + C::NH;
   uint64_t *empty_t = full_t + C::NT;
-  volatile int *sflag = reinterpret_cast<volatile int *>(empty_t + C::NT);  // [NT]: s loaded
+  uint64_t *never = empty_t + C::NT;  // completed by nothing: the zero wait limit's first wait
+  volatile int *sflag = reinterpret_cast<volatile int *>(never + 1);  // [NT]: s loaded
   volatile int *abort_flag = sflag + C::NT;
 
   const int tid = threadIdx.x;
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
       mbar_init(&full_t[i], 1);
       mbar_init(&empty_t[i], W);
     }
+    mbar_init(never, 1);
     *abort_flag = 0;
     mbar_init_fence();
   }
@@ -306,9 +308,8 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
     int tx, ty, z0, z1, dir;
     item_geom(item, tx, ty, z0, z1, dir);
     if (z0 >= z1) continue;
-    // with a zero wait limit, look at the item's first copy before anything else
-    // (it is normally still in flight then) and give up if it has not landed
-    if (a.wait_ns == 0) mbar_wait_first(&full_t[tpos & (C::NT - 1)], (tpos / C::NT) & 1, abort_flag, 0);
+    // a zero wait limit gives up here, on a barrier that nothing completes
+    if (a.wait_ns == 0) mbar_wait_first(never, 0, abort_flag, 0);
     auto phys = [&](int p) -> int { return dir > 0 ? p : z0 + z1 - 1 - p; };
     const int gx = a.bx0 + tx * TX + NX * lane;
     const int y0 = a.by0 + ty * TY;

@@ -118,9 +118,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
   }
 }
 
-// The first wait of a work item: as mbar_wait_bounded, but with limit_ns = 0 the
-// first look does not block (a try_wait may suspend until the phase completes), so
-// that a zero limit gives up at the first copy still in flight.
+// As mbar_wait_bounded, but with limit_ns = 0 the look does not block (a try_wait
+// may suspend until the phase completes): a phase not complete at once gives up.
 __device__ __forceinline__ bool mbar_wait_first(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
                                                 uint64_t limit_ns) {
   if (limit_ns == 0 && !mbar_test_wait(bar, parity)) {
