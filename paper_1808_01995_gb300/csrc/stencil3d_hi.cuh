@@ -318,11 +318,17 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
     for (int i = 0; i < NX; ++i) nin += gx + i < a.bx1 ? 1 : 0;
     bool yin[NY];
     int rofs[NY];  // in-plane offset of each row (row clamped inside the grid)
+    // this lane's first point of each row in plane 0 of the output (and gradient):
+    // a plane's store address is then one 64-bit add
+    float *obase[NY];
+    float *gbase[NY];
 #pragma unroll
     for (int r = 0; r < NY; ++r) {
       const int gy = y0 + ty0 + r;
       yin[r] = gy < a.by1;
       rofs[r] = min(gy, a.g.ny - 1) * a.g.pitch;
+      obase[r] = a.out + rofs[r] + gx;
+      gbase[r] = MODE == kModeAdjGrad ? a.grad + rofs[r] + gx : nullptr;
     }
 
     // z queue: q[r][p][o + j] = u^n at plane z - R + j (o = offset of the plane in an
@@ -449,8 +455,8 @@ __global__ void __launch_bounds__(CfgHi<R, MODE>::THREADS, 1)
         if (yin[r] && nin > 0 && live &&
             WP_IN_BOUNDS(pz >= 0 && pz < a.g.nz && y0 + ty0 + r < a.g.ny && gx >= 0 && gx + nin - 1 < a.g.nx,
                          a.err)) {
-          float *op = a.out + po + rofs[r] + gx;
-          float *gp = a.grad + po + rofs[r] + gx;
+          float *op = obase[r] + po;
+          float *gp = gbase[r] + po;
           if (nin == NX) {
             stp(op, un);
             if (MODE == kModeAdjGrad) stp(gp, gn);
