@@ -101,8 +101,9 @@ struct wp_ctx {
   // while that one still runs (its blocks wait for it on the device), hiding the
   // launch gaps between the stencil, injection and interpolation of a step.
   // pdl_mode: 0 never, 1 (default) at every order, 2 only with the stencil kernel
-  // of half-orders up to 4.  Measured on 336^3 shots of 1000 steps: SO16 1.5 us
-  // less per step, SO8 within the noise of 1 us.
+  // of half-orders up to 4.  Measured: the 280^3 SO8 gradient (plain launches)
+  // 437 -> 412 ms; 336^3 shots of 1000 steps (replayed graphs) SO16 1.5 us less
+  // per step, SO8 within the noise of 1 us.
   int pdl_mode = 1;
   bool pdl_scope = false;  // inside a time loop that uses it
   bool chain = false;      // the last operation enqueued was a step kernel
