@@ -14,7 +14,6 @@
 import hashlib
 import os
 
-import numpy as np
 import pytest
 
 import bench
