@@ -509,7 +509,9 @@ def wp_checkpoint_schedule(nt: int, checkpoints: int):
 
 
 def wp_set_wait_limit(ctx: int, seconds: float) -> None:
-    """Limit of the stencil kernels' internal waits (default 2 s; 0: give up unless complete)."""
+    """Limit of the stencil kernels' internal waits (default 2 s, at most 60). 0 makes
+    every stencil kernel give up at the start of its first work item (the failure
+    path, deterministically): the call then returns WP_EDEVICE."""
     _check(lib().wp_set_wait_limit(ctx, float(seconds)))
 
 
